@@ -1,0 +1,245 @@
+"""Seeded synthetic inputs for the gridding workloads.
+
+This module only synthesises inputs (sample coordinates, channel data, target
+coordinates and kernel parameters).  It contains none of the gridding
+arithmetic, so both the CUDA path and the FP64 oracle can consume it.
+
+All randomness comes from ``numpy.random.Generator(PCG64(seed))`` with
+``seed = 1604_06667 + config id`` unless overridden.
+
+Workloads (sizes at ``scale = 1``):
+
+* ``plain2d``  -- 20,000 samples uniform in a 5 x 5 deg field at (30, 0); value =
+  5 Gaussian sources (FWHM 6', amplitude U[1,10]) + N(0, 0.1) noise; unit
+  weights; 100 x 100 plate-carree targets at 3'; gauss1d sigma = 2.5',
+  support 3 sigma, hpx_maxres = sigma / 2.  (The shape of the paper's
+  Example 1, Sect. 4: uniform random positions and a noise-like signal.)
+* ``cube``     -- 1e6 samples on a basket-weave raster (1' rows, 0.5' along scan,
+  pointing jitter N(0, 0.2')) over lon 115-125, lat 25-35; 256 channels
+  (3 Gaussian lines of width 5 channels with spatially smooth amplitude,
+  + N(0,1) noise); 512 x 512 targets; gauss1d sigma = 3', support 9'.
+* ``allsky``   -- 1e7 samples uniform on the sphere (poles included); 32
+  channels of smooth random fields (16 blobs of FWHM 5 deg shared by all
+  channels with per-channel amplitudes) + N(0, 0.1); 4096 x 2048 full-sky
+  plate-carree targets (pixel centres off the poles, longitude wrap);
+  elliptical Gaussian sigma_maj = 10', sigma_min = 6', PA = 30 deg, support
+  3 sigma_maj, hpx_maxres = sigma_min / 2.
+* ``diff``     -- 2e5 samples uniform in 512' x 512' at (200, -20); 16 channels;
+  256 x 256 targets at 2'; sigma = 4', support 12'.
+
+``scale < 1`` shrinks a workload for fast parity tests while keeping its
+sample density, pixel size and kernel (field side scales as sqrt(scale)).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 1604_06667
+ARCMIN = 1.0 / 60.0
+
+
+@dataclass
+class Workload:
+    name: str
+    lon_s: np.ndarray            # float64 [N] degrees
+    lat_s: np.ndarray            # float64 [N] degrees
+    data: np.ndarray             # float32 [N][C]
+    omega: np.ndarray | None     # float32 [N] or None (unit weights)
+    lon_t: np.ndarray            # float64 [P] degrees
+    lat_t: np.ndarray            # float64 [P] degrees
+    kernel: dict                 # {"type": "gauss1d", "sigma": deg, ...}
+    support: float               # degrees
+    hpx_maxres: float            # degrees
+    grid_shape: tuple = ()       # (ny, nx) of the plate-carree target grid
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.lon_s.size)
+
+    @property
+    def n_targets(self) -> int:
+        return int(self.lon_t.size)
+
+    @property
+    def n_channels(self) -> int:
+        return int(self.data.shape[1])
+
+
+def rng_for(cid: int, seed: int | None = None) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + cid if seed is None else seed))
+
+
+def car_grid(lon0: float, lat0: float, nx: int, ny: int, dpix: float):
+    """Plate-carree target centres around (lon0, lat0), row-major (lat outer)."""
+    xs = lon0 + (np.arange(nx) - 0.5 * (nx - 1)) * dpix
+    ys = lat0 + (np.arange(ny) - 0.5 * (ny - 1)) * dpix
+    lat, lon = np.meshgrid(ys, xs, indexing="ij")
+    return lon.ravel().astype(np.float64), lat.ravel().astype(np.float64)
+
+
+def allsky_car(nx: int, ny: int):
+    """Full-sky plate-carree pixel centres; none sits on a pole."""
+    xs = (np.arange(nx) + 0.5) * (360.0 / nx)
+    ys = -90.0 + (np.arange(ny) + 0.5) * (180.0 / ny)
+    lat, lon = np.meshgrid(ys, xs, indexing="ij")
+    return lon.ravel().astype(np.float64), lat.ravel().astype(np.float64)
+
+
+def _flat_gauss(lon, lat, lon_k, lat_k, sigma):
+    dx = (lon - lon_k) * math.cos(math.radians(lat_k))
+    dy = lat - lat_k
+    return np.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma))
+
+
+def plain2d(scale: float = 1.0, seed: int | None = None) -> Workload:
+    rng = rng_for(1, seed)
+    side = 5.0 * math.sqrt(scale)
+    n = max(1, int(round(20_000 * scale)))
+    lon0, lat0 = 30.0, 0.0
+    lon = lon0 + (rng.random(n) - 0.5) * side
+    lat = lat0 + (rng.random(n) - 0.5) * side
+    sig_src = 6.0 * ARCMIN / math.sqrt(8.0 * math.log(2.0))
+    val = rng.normal(0.0, 0.1, n)
+    for _ in range(5):
+        lk = lon0 + (rng.random() - 0.5) * side
+        bk = lat0 + (rng.random() - 0.5) * side
+        val += rng.uniform(1.0, 10.0) * _flat_gauss(lon, lat, lk, bk, sig_src)
+    npx = max(2, int(round(100 * math.sqrt(scale))))
+    lon_t, lat_t = car_grid(lon0, lat0, npx, npx, 3.0 * ARCMIN)
+    sigma = 2.5 * ARCMIN
+    return Workload("plain2d", lon, lat, val.astype(np.float32)[:, None], None, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, sigma / 2.0,
+                    (npx, npx), {"scale": scale})
+
+
+def _raster(rng, lon_lo, lat_lo, side, n_total, row_step, scan_step, jitter):
+    """Basket-weave raster: zig-zag scans along longitude, then along latitude,
+    truncated at ``n_total`` samples."""
+    nrow = max(1, int(round(side / row_step)))
+    nalong = max(1, int(round(side / scan_step)))
+    rows = lat_lo + (np.arange(nrow) + 0.5) * row_step
+    along = lon_lo + (np.arange(nalong) + 0.5) * scan_step
+    # pass 1: scans of constant latitude
+    lat1 = np.repeat(rows, nalong)
+    lon1 = np.tile(along, nrow).reshape(nrow, nalong)
+    lon1[1::2] = lon1[1::2, ::-1]
+    lon1 = lon1.ravel()
+    # pass 2: scans of constant longitude
+    cols = lon_lo + (np.arange(nrow) + 0.5) * row_step
+    along2 = lat_lo + (np.arange(nalong) + 0.5) * scan_step
+    lon2 = np.repeat(cols, nalong)
+    lat2 = np.tile(along2, nrow).reshape(nrow, nalong)
+    lat2[1::2] = lat2[1::2, ::-1]
+    lat2 = lat2.ravel()
+    lon = np.concatenate([lon1, lon2])[:n_total]
+    lat = np.concatenate([lat1, lat2])[:n_total]
+    lon = lon + rng.normal(0.0, jitter, lon.size)
+    lat = lat + rng.normal(0.0, jitter, lat.size)
+    return lon, lat
+
+
+def cube(scale: float = 1.0, seed: int | None = None, n_channels: int = 256) -> Workload:
+    rng = rng_for(2, seed)
+    side = 10.0 * math.sqrt(scale)
+    n = max(1, int(round(1_000_000 * scale)))
+    lon_lo, lat_lo = 120.0 - 0.5 * side, 30.0 - 0.5 * side
+    lon, lat = _raster(rng, lon_lo, lat_lo, side, n, 1.0 * ARCMIN, 0.5 * ARCMIN,
+                       0.2 * ARCMIN)
+    C = n_channels
+    # spatially smooth line amplitude: a few broad blobs
+    amp = np.zeros(lon.size)
+    for _ in range(6):
+        lk = lon_lo + rng.random() * side
+        bk = lat_lo + rng.random() * side
+        amp += rng.uniform(1.0, 10.0) * _flat_gauss(lon, lat, lk, bk, 0.15 * side + 0.05)
+    chan = np.arange(C, dtype=np.float32)
+    sig_ch = 5.0 / math.sqrt(8.0 * math.log(2.0))
+    data = rng.standard_normal((lon.size, C), dtype=np.float32)
+    for _ in range(3):
+        c0 = rng.uniform(0.08 * C, 0.92 * C)
+        prof = np.exp(-((chan - c0) ** 2) / (2.0 * sig_ch * sig_ch)).astype(np.float32)
+        data += (amp.astype(np.float32) * rng.uniform(0.3, 1.0))[:, None] * prof[None, :]
+    npx = max(2, int(round(512 * math.sqrt(scale))))
+    lon_t, lat_t = car_grid(120.0, 30.0, npx, npx, side / npx)
+    sigma = 3.0 * ARCMIN
+    return Workload("cube", lon, lat, data, None, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, sigma / 2.0,
+                    (npx, npx), {"scale": scale})
+
+
+def allsky(scale: float = 1.0, seed: int | None = None, n_channels: int = 32) -> Workload:
+    rng = rng_for(3, seed)
+    n = max(1, int(round(10_000_000 * scale)))
+    z = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 360.0, n)
+    lat = np.degrees(np.arcsin(z))
+    lon = phi
+    C = n_channels
+    nb = 16
+    bz = rng.uniform(-1.0, 1.0, nb)
+    bphi = rng.uniform(0.0, 2.0 * math.pi, nb)
+    bs = np.sqrt(1.0 - bz * bz)
+    bvec = np.stack([bs * np.cos(bphi), bs * np.sin(bphi), bz], axis=1)      # [nb, 3]
+    sig_b = math.radians(5.0) / math.sqrt(8.0 * math.log(2.0))
+    kappa = 1.0 / (sig_b * sig_b)
+    A = rng.uniform(-5.0, 5.0, (nb, C)).astype(np.float32)
+    data = np.empty((n, C), dtype=np.float32)
+    step = 1 << 20
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        cz = z[s:e]
+        cs = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+        cp = np.radians(phi[s:e])
+        u = np.stack([cs * np.cos(cp), cs * np.sin(cp), cz], axis=1)
+        B = np.exp(kappa * (u @ bvec.T - 1.0)).astype(np.float32)            # [m, nb]
+        data[s:e] = B @ A + rng.normal(0.0, 0.1, (e - s, C)).astype(np.float32)
+    nx = max(4, int(round(4096 * math.sqrt(scale))))
+    ny = max(2, nx // 2)
+    lon_t, lat_t = allsky_car(nx, ny)
+    smaj, smin = 10.0 * ARCMIN, 6.0 * ARCMIN
+    return Workload("allsky", lon, lat, data, None, lon_t, lat_t,
+                    {"type": "gauss2d", "smaj": smaj, "smin": smin, "pa": 30.0},
+                    3.0 * smaj, smin / 2.0, (ny, nx), {"scale": scale})
+
+
+def diff(scale: float = 1.0, seed: int | None = None) -> Workload:
+    rng = rng_for(5, seed)
+    side = 512.0 * ARCMIN * math.sqrt(scale)
+    n = max(1, int(round(200_000 * scale)))
+    lon0, lat0 = 200.0, -20.0
+    lon = lon0 + (rng.random(n) - 0.5) * side
+    lat = lat0 + (rng.random(n) - 0.5) * side
+    C = 16
+    data = rng.normal(0.0, 1.0, (n, C)).astype(np.float32)
+    for _ in range(8):
+        lk = lon0 + (rng.random() - 0.5) * side
+        bk = lat0 + (rng.random() - 0.5) * side
+        prof = _flat_gauss(lon, lat, lk, bk, 10.0 * ARCMIN).astype(np.float32)
+        data += prof[:, None] * rng.uniform(1.0, 10.0, C).astype(np.float32)[None, :]
+    npx = max(2, int(round(256 * math.sqrt(scale))))
+    lon_t, lat_t = car_grid(lon0, lat0, npx, npx, 2.0 * ARCMIN)
+    sigma = 4.0 * ARCMIN
+    return Workload("diff", lon, lat, data, None, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, sigma / 2.0,
+                    (npx, npx), {"scale": scale})
+
+
+def random_field(cid: int, n: int, n_targets_side: int, C: int, lon0: float, lat0: float,
+                 side_deg: float, sigma_deg: float, seed: int | None = None,
+                 weights: bool = False) -> Workload:
+    """Small generic case for edge tests: uniform samples in a square field."""
+    rng = rng_for(cid, seed)
+    lon = lon0 + (rng.random(n) - 0.5) * side_deg
+    lat = np.clip(lat0 + (rng.random(n) - 0.5) * side_deg, -90.0, 90.0)
+    data = rng.normal(0.0, 1.0, (n, C)).astype(np.float32) + 3.0
+    om = rng.uniform(0.2, 2.0, n).astype(np.float32) if weights else None
+    lon_t, lat_t = car_grid(lon0, lat0, n_targets_side, n_targets_side,
+                            side_deg / n_targets_side)
+    lat_t = np.clip(lat_t, -90.0, 90.0)
+    return Workload("random", lon, lat, data, om, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": sigma_deg}, 3.0 * sigma_deg,
+                    sigma_deg / 2.0, (n_targets_side, n_targets_side), {})

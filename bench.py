@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: convolution gridding (Winkel, Lenz & Floeer 2016) on GB300.
+
+Workload: the spectral cube -- 1e6 samples on a basket-weave raster over
+10 x 10 deg, 256 channels per sample, gridded onto 512 x 512 plate-carree
+targets with a Gaussian kernel of sigma = 3', support 9', HEALPix nside 4096
+(hpx_maxres = sigma / 2).  Inputs are synthetic and seeded (workloads.cube).
+
+One step = one full pass of the hot path over the batch, through the C ABI
+(cg_grid_oneshot): sample HEALPix keys, radix sort, sample gather / ring
+offsets / tile ranges, tile gridder, normalisation into the [P][C] cube.
+Inputs are resident in HBM at the start of the timed region and are larger
+than L2 (1 GB of FP32 data / 512 MB of BF16), so no flush is needed.
+
+Metric: sample-channel kernel updates per second = C x #{(p, n): d_pn <= r}
+per step / step time; the pair count comes from the library's own count of
+the cut decisions and is checked against the FP64 oracle's count stored in
+tests/golden/pair_counts.json.
+
+`--impl reference` times the FP64 CPU oracle (the HEALPix-lookup gridder of
+oracle/) on bounded samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sample·channel kernel updates/s and % HBM roofline, mixed vs FP32 form"
+UNIT = "updates/s"
+GOLDEN_PAIRS = os.path.join(ROOT, "tests", "golden", "pair_counts.json")
+FFMA_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["auto", "fp32", "bf16"], default="auto")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=12000)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def golden_pairs(name):
+    if not os.path.exists(GOLDEN_PAIRS):
+        return None
+    with open(GOLDEN_PAIRS) as f:
+        return json.load(f).get(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_desc(wl, form):
+    return ("spectral cube: %d samples x %d channels (basket-weave raster, 10x10 deg) -> "
+            "%dx%d plate-carree targets; gauss1d sigma=3', support 9', nside 4096; %s data"
+            % (wl.n_samples, wl.n_channels, wl.grid_shape[1], wl.grid_shape[0],
+               "BF16" if form == "bf16" else "FP32"))
+
+
+def algorithmic_bytes(wl, data_bytes):
+    """Bytes the method must move once per step: sample coordinates (FP64 lon,
+    lat) and data rows read once; the map and weight map written once."""
+    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
+    return N * (16 + C * data_bytes) + P * (C * 4 + 4)
+
+
+def cpu_oracle_rate(wl, n_sub, seed=12345):
+    """Time the FP64 lookup oracle as it stands on a random subset of the
+    workload's samples (all targets).  Returns (updates/s, seconds, sample)."""
+    import numpy as np
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.sort(rng.choice(wl.n_samples, size=min(n_sub, wl.n_samples), replace=False))
+    ns = oracle.nside_for_resolution(wl.hpx_maxres)
+    k = oracle.gauss1d(wl.kernel["sigma"], wl.support)
+    d64 = wl.data[idx].astype(np.float64)
+    t0 = time.perf_counter()
+    res = oracle.grid_lookup(ns, wl.lon_t, wl.lat_t, wl.lon_s[idx], wl.lat_s[idx], d64, k)
+    dt = time.perf_counter() - t0
+    upd = res.npairs * wl.n_channels
+    return upd / dt, dt, idx.size, res.npairs
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import workloads
+    wl = workloads.cube(scale=args.scale)
+    form = "fp32" if args.form == "auto" else args.form
+    n_sub = max(200, args.cpu_samples // 4)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, max(50, n_sub // 10), seed=7)
+    tot_upd, tot_t = 0.0, 0.0
+    for s in range(args.steps):
+        rate, dt, n, pairs = cpu_oracle_rate(wl, n_sub, seed=1000 + s)
+        tot_upd += pairs * wl.n_channels
+        tot_t += dt
+    value = tot_upd / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(wl, form), "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d random samples of the workload per step, all %d targets"
+                                   % (n_sub, wl.n_targets)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder, _capi
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peaks_src = load_peaks()
+    wl = workloads.cube(scale=args.scale)
+    form = "fp32" if args.form == "auto" else args.form
+    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
+    lon = torch.from_numpy(wl.lon_s).to(dev)
+    lat = torch.from_numpy(wl.lat_s).to(dev)
+    data32 = torch.from_numpy(wl.data).to(dev)
+    data = data32.to(torch.bfloat16) if form == "bf16" else data32
+    dbytes = 2 if form == "bf16" else 4
+    if form == "bf16":
+        del data32
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=C, device=dev)
+    g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
+    out = torch.empty((P, C), device=dev, dtype=torch.float32)
+    out_w = torch.empty(P, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        g.grid_oneshot(lon, lat, data, out=out, out_weights=out_w)
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+    info0 = g.info()
+    pairs = info0["n_pairs"]
+    gold = golden_pairs("cube_scale%g" % args.scale)
+
+    # ---- timed region (device-resident inputs) ----
+    g.set_timing(True)
+    g.read_timing()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stages = g.read_timing()
+    g.set_timing(False)
+    info1 = g.info()
+    launches = info1["n_launches"] - info0["n_launches"]
+    ms_max = max_over_ranks(ms, world)
+    upd_per_step = float(pairs) * C
+    value = upd_per_step * world / (ms_max / 1e3)
+
+    # dominant kernel: the tile gridder
+    t_grid = stages["grid"] / max(1, stages["grid_launches"])
+    fma_flops = 2.0 * upd_per_step
+    if form == "fp32":
+        peak_tf = N_SMS * FFMA_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach_tf = fma_flops / (t_grid / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach_tf / peak_tf, "traffic": None,
+                "kernel": "k_grid_f32 (tile gridder, FP32 CUDA cores)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    else:
+        hbm = peaks["hbm_gbs"]
+        gbytes = algorithmic_bytes(wl, dbytes) / 1e9
+        ach = gbytes / (t_grid / 1e3)
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "tile gridder (BF16 tensor cores)",
+                "peak_source": peaks_src}
+    step_bytes = algorithmic_bytes(wl, dbytes)
+    hbm_frac = step_bytes / (ms_max / 1e3) / 1e9 / peaks["hbm_gbs"]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if form == "bf16" else "f32",
+        "data": "synthetic (seeded basket-weave raster cube; no dataset)",
+        "config": {"workload": workload_desc(wl, form), "form": form,
+                   "l2": "inputs larger than L2 (%d MB of channel data), no flush"
+                         % (N * C * dbytes // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pairs_per_step": pairs,
+        "pairs_oracle": gold,
+        "hbm_roofline": {"bytes_per_step": step_bytes,
+                         "achieved_gbs": step_bytes / (ms_max / 1e3) / 1e9,
+                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_frac,
+                         "peak_source": peaks_src},
+        "roofline": roof,
+        "stages_ms_per_step": {k: v / args.steps for k, v in stages.items()
+                               if k != "grid_launches"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    # ---- end to end: pinned host inputs, copies inside the timed region ----
+    if not args.no_e2e:
+        h_lon = torch.from_numpy(wl.lon_s).pin_memory()
+        h_lat = torch.from_numpy(wl.lat_s).pin_memory()
+        h_data = data.cpu().pin_memory()
+        h_out = torch.empty((P, C), dtype=torch.float32).pin_memory()
+        d_lon, d_lat, d_data = torch.empty_like(lon), torch.empty_like(lat), torch.empty_like(data)
+
+        def e2e_step():
+            d_lon.copy_(h_lon, non_blocking=True)
+            d_lat.copy_(h_lat, non_blocking=True)
+            d_data.copy_(h_data, non_blocking=True)
+            g.grid_oneshot(d_lon, d_lat, d_data, out=out, out_weights=out_w)
+            h_out.copy_(out, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+        hb = N * 16 + N * C * dbytes
+        line["e2e"] = {"value": upd_per_step * world / (ms_e2e / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": hb, "d2h_bytes_per_step": P * C * 4,
+                       "ms_per_step": ms_e2e}
+
+    # ---- CPU baseline: the FP64 oracle as it stands, rank 0 only ----
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, dt, n, npairs = cpu_oracle_rate(wl, args.cpu_samples)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%d random samples of the workload (%d pairs, %d "
+                                          "channels) onto all %d targets, %.1f s"
+                                          % (n, npairs, C, P, dt)}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

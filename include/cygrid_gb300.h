@@ -1,0 +1,205 @@
+/*
+ * cygrid_gb300.h -- C ABI of the GB300 convolution-gridding library.
+ *
+ * The library grids irregularly sampled sky data (one value or a spectrum of
+ * C channels per sample) onto arbitrary target coordinates by convolution
+ * with a kernel, following Winkel, Lenz & Floeer (A&A 2016), Sect. 2:
+ *
+ *   numerator  N_pc = sum_n omega_n w(p, n) D_nc         (Eq. 1)
+ *   weight map W_p  = sum_n omega_n w(p, n)              (Eq. 2)
+ *   map        R_pc = N_pc / W_p   (NaN where W_p = 0)   (Eq. 3)
+ *
+ * with the sum restricted to samples within the support radius r of the
+ * target (d <= r, Sect. 3.5).  Candidate samples are found with the paper's
+ * HEALPix lookup (Sect. 2.2, 3.3): the samples' RING indices, a stable sort
+ * of the samples by index, and a disc query around each tile of targets.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Angles are in degrees: longitude (any real value, folded into [0,360))
+ *    and latitude in [-90, 90]; kernel sizes and the support radius too.
+ *  - Every array argument is a pointer to DEVICE memory of the current CUDA
+ *    device, owned by the caller, contiguous, and must stay valid until the
+ *    work enqueued by the call has executed on the handle's stream.  The
+ *    library never frees caller memory.  Exceptions are marked "host".
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on the handle's stream and return without
+ *    waiting, except where a call is documented as synchronising.
+ *  - The handle owns its workspace (allocated with stream-ordered
+ *    cudaMallocAsync and released by cg_grid_destroy).  A handle must not be
+ *    used from two host threads at once.
+ *  - Errors: every call returns a cg_status.  Argument errors are detected on
+ *    the host and returned at once; the message is available from
+ *    cg_last_error() (thread-local).  Errors that only the device can see
+ *    (non-finite or out-of-range sample coordinates) set a device error word
+ *    that the next synchronising call (cg_grid_finalize, cg_sync) reports as
+ *    CG_EINVAL or CG_EDEVICE.  Nothing in the library traps, aborts or
+ *    asserts on the device.
+ */
+#ifndef CYGRID_GB300_H
+#define CYGRID_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cg_grid cg_grid; /* opaque, library-owned */
+
+typedef enum {
+  CG_OK = 0,
+  CG_EINVAL = 1,    /* invalid argument or invalid input value */
+  CG_ENOMEM = 2,    /* device allocation failed */
+  CG_ECUDA = 3,     /* a CUDA runtime call failed */
+  CG_EDEVICE = 4,   /* the device reported an internal error */
+  CG_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  CG_ESTATE = 6     /* call not valid in the handle's current state */
+} cg_status;
+
+typedef enum { CG_F32 = 0, CG_BF16 = 1 } cg_dtype;
+
+typedef enum {
+  CG_GAUSS1D = 0, /* params[0] = sigma (deg): w = exp(-d^2 / (2 sigma^2)) */
+  CG_GAUSS2D = 1  /* params = {sigma_maj, sigma_min, PA} (deg), PA of the
+                     major axis from north through east; with beta the
+                     bearing of the sample seen from the target,
+                     a = d cos(beta - PA), b = d sin(beta - PA),
+                     w = exp(-a^2/(2 sigma_maj^2) - b^2/(2 sigma_min^2)) */
+} cg_kernel;
+
+typedef enum {
+  CG_PATH_AUTO = 0, /* choose by channel count and data type */
+  CG_PATH_FP32 = 1, /* channel accumulation on FP32 CUDA cores */
+  CG_PATH_TC = 2    /* BF16 x BF16 -> FP32 on the tcgen05 tensor cores */
+} cg_path;
+
+/* Create a gridder for n_targets target directions (paper Sect. 3.5: WcsGrid
+ * / SlGrid -- here always an explicit list of sight lines).
+ *   out        host: receives the new handle.
+ *   lon_deg,
+ *   lat_deg    device, [n_targets] float64 each.
+ *   n_targets  1 .. 2^31-1.
+ *   n_channels C >= 1, the length of each sample's spectrum.
+ *   stream     cudaStream_t (as void*) for all work of this handle.
+ * Target geometry (unit vectors, tiles of nearby targets) is computed here,
+ * on the stream.  Invalid target coordinates return CG_EINVAL after a
+ * synchronisation of the stream (create is a set-up call and synchronises). */
+cg_status cg_grid_create(cg_grid** out, const double* lon_deg, const double* lat_deg,
+                         int64_t n_targets, int32_t n_channels, void* stream);
+
+/* Set the kernel (paper Sect. 3.5, set_kernel).
+ *   kernel_type   cg_kernel.
+ *   params        host, [n_params]: {sigma} or {sigma_maj, sigma_min, PA}, degrees.
+ *   support_deg   support radius r > 0: samples with d > r do not contribute.
+ *   nside         internal HEALPix resolution (power of two, 1 .. 8192), or 0 to
+ *                 derive it from hpx_maxres_deg: the smallest power of two with
+ *                 pixel size sqrt(pi/3)/nside <= hpx_maxres_deg.
+ * The result does not depend on nside (the cut d <= r is exact); nside only
+ * changes how candidates are found.  Resets the accumulators.  Synchronising. */
+cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params,
+                        int32_t n_params, double support_deg, int32_t nside,
+                        double hpx_maxres_deg);
+
+/* Accumulate samples into the numerator and weight map (Eq. 1-2; paper
+ * Sect. 2.1 algorithm, step 2).  Multiple calls accumulate (streaming).
+ *   lon_deg, lat_deg  device, [n_samples] float64.
+ *   data              device, [n_samples][C] row-major, dtype data_dtype.
+ *   data_dtype        CG_F32 or CG_BF16.
+ *   weights           device, [n_samples] float32 >= 0, or NULL for unit weights.
+ *   n_samples         0 .. 2^31-1 (0 is a no-op).
+ * Asynchronous.  Non-finite or |lat| > 90 coordinates are reported by the
+ * next synchronising call as CG_EINVAL. */
+cg_status cg_grid_add(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                      const void* data, int32_t data_dtype, const float* weights,
+                      int64_t n_samples);
+
+/* Normalise (Eq. 3; paper Sect. 2.1 step 3, get_datacube) without changing
+ * the accumulators.
+ *   out                  device float32: [n_targets][C] (layout 0) or
+ *                        [C][n_targets] (layout 1, the FITS cube order).
+ *   out_weights          device float32 [n_targets] (W_p), or NULL.
+ * NaN where W_p = 0.  Synchronises the stream and reports device errors. */
+cg_status cg_grid_finalize(cg_grid* g, float* out, int32_t layout_channel_major,
+                           float* out_weights);
+
+/* One-shot gridding: reset, add, finalize in one call (paper Listing 1:
+ * grid() followed by get_datacube()).  Arguments as for cg_grid_add and
+ * cg_grid_finalize.  Does NOT synchronise: device errors are reported by the
+ * next cg_sync or cg_grid_finalize. */
+cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                          const void* data, int32_t data_dtype, const float* weights,
+                          int64_t n_samples, float* out, int32_t layout_channel_major,
+                          float* out_weights);
+
+/* Zero the accumulators (asynchronous). */
+cg_status cg_grid_reset(cg_grid* g);
+
+/* Release the handle and its workspace (synchronises the stream). */
+cg_status cg_grid_destroy(cg_grid* g);
+
+/* Change the stream used by later calls. */
+cg_status cg_set_stream(cg_grid* g, void* stream);
+
+/* Select the channel-accumulation form (cg_path). */
+cg_status cg_set_path(cg_grid* g, int32_t path);
+
+/* Wait for the handle's stream and report device-side errors. */
+cg_status cg_sync(cg_grid* g);
+
+/* Thread-local description of the last error ("" if none). */
+const char* cg_last_error(void);
+
+/* Counters and layout facts of a handle (host struct).
+ *   nside, n_tiles, tile_size, n_ranges: planner choices;
+ *   pairs_tested: (target, candidate) pairs the last add evaluated;
+ *   path: the accumulation form the last add used (cg_path). */
+typedef struct {
+  int64_t n_targets;
+  int32_t n_channels;
+  int32_t nside;
+  int64_t n_tiles;
+  int32_t tile_size;
+  int32_t path;
+  int64_t n_ranges;
+  int64_t n_samples_total;
+  int64_t n_pairs;      /* (target, sample) pairs with d <= r since the last reset */
+  int64_t n_launches;   /* kernels this handle has launched since creation */
+} cg_info;
+/* Fill *info (host struct).  Synchronises the stream (n_pairs is device-side). */
+cg_status cg_get_info(cg_grid* g, cg_info* info);
+
+/* Stage timing with CUDA events recorded on the handle's stream.
+ * Stages: 0 sample keys (ang2pix), 1 radix sort, 2 sample gather + ring
+ * offsets + tile sample ranges, 3 tile gridder, 4 normalisation / layout.
+ * When enabled, every add / oneshot / finalize records its stages.
+ * cg_read_timing waits for the stream, writes the summed milliseconds per
+ * stage (host array ms[CG_N_STAGES]) over all calls recorded since the
+ * previous read and the number of gridder launches, then clears the record. */
+#define CG_N_STAGES 5
+cg_status cg_set_timing(cg_grid* g, int32_t enable);
+cg_status cg_read_timing(cg_grid* g, double* ms, int64_t* n_grid_launches);
+
+/* RING-scheme HEALPix index of each direction (paper Sect. 2.2 step 3a; the
+ * tessellation of Gorski et al. 2005).
+ *   lon_deg, lat_deg  device [n] float64.   pix  device [n] int64.
+ * Invalid coordinates give pix = -1.  Asynchronous on `stream`. */
+cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* lat_deg,
+                          int64_t n, int64_t* pix, void* stream);
+
+/* Copy out the sample index built by the last cg_grid_add (the sorted
+ * replacement for the paper's hash tables, Sect. 3.4):
+ *   sorted_pix  device [n] int64: RING indices in ascending order;
+ *   perm        device [n] int64: original sample index of each sorted entry
+ *               (ties in ascending original order: a stable sort);
+ *   ring_off    device [4 nside + 1] int64: first sorted position whose pixel
+ *               lies in ring >= i (ring 0 and 4 nside are sentinels), or NULL.
+ * n must equal the sample count of that add.  Asynchronous. */
+cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
+                               int64_t* ring_off, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CYGRID_GB300_H */

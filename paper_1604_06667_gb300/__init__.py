@@ -1,0 +1,17 @@
+"""GB300-native convolution gridding (Winkel, Lenz & Floeer 2016, arXiv 1604.06667).
+
+The compute path is the CUDA library behind the C ABI in include/cygrid_gb300.h;
+this package is its thin Python binding.  Submodules load lazily so that
+``import paper_1604_06667_gb300`` works on machines without a GPU.
+"""
+__all__ = ["Gridder", "ang2pix_ring", "build"]
+
+
+def __getattr__(name):
+    if name in ("Gridder", "ang2pix_ring"):
+        from . import gridder
+        return getattr(gridder, name)
+    if name == "build":
+        from .build import build
+        return build
+    raise AttributeError(name)

@@ -1,0 +1,119 @@
+"""ctypes declarations of the C ABI in include/cygrid_gb300.h (same names).
+
+Argument marshalling only: every step of the gridding runs in the CUDA
+library.  There is no fallback: if the library has not been built, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcygrid_gb300.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_EDEVICE, CG_ETIMEOUT, CG_ESTATE = range(7)
+CG_F32, CG_BF16 = 0, 1
+CG_GAUSS1D, CG_GAUSS2D = 0, 1
+CG_PATH_AUTO, CG_PATH_FP32, CG_PATH_TC = 0, 1, 2
+
+STATUS_NAMES = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_EDEVICE",
+                5: "CG_ETIMEOUT", 6: "CG_ESTATE"}
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("n_targets", ctypes.c_int64), ("n_channels", ctypes.c_int32),
+                ("nside", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
+                ("tile_size", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("n_ranges", ctypes.c_int64), ("n_samples_total", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("n_launches", ctypes.c_int64)]
+
+CG_N_STAGES = 5
+STAGE_NAMES = ("keys", "sort", "index", "grid", "finalize")
+
+
+class CygridError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_dbl = ctypes.c_double
+
+# name -> argtypes; every function returns cg_status (int) except cg_last_error
+SIGNATURES = {
+    "cg_grid_create": [ctypes.POINTER(_vp), _vp, _vp, _i64, _i32, _vp],
+    "cg_set_kernel": [_vp, _i32, ctypes.POINTER(_dbl), _i32, _dbl, _i32, _dbl],
+    "cg_grid_add": [_vp, _vp, _vp, _vp, _i32, _vp, _i64],
+    "cg_grid_finalize": [_vp, _vp, _i32, _vp],
+    "cg_grid_oneshot": [_vp, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _i32, _vp],
+    "cg_grid_reset": [_vp],
+    "cg_grid_destroy": [_vp],
+    "cg_set_stream": [_vp, _vp],
+    "cg_set_path": [_vp, _i32],
+    "cg_sync": [_vp],
+    "cg_get_info": [_vp, ctypes.POINTER(CgInfo)],
+    "cg_ang2pix_ring": [_i32, _vp, _vp, _i64, _vp, _vp],
+    "cg_grid_export_index": [_vp, _vp, _vp, _vp, _i64],
+    "cg_set_timing": [_vp, _i32],
+    "cg_read_timing": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)],
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libcygrid_gb300.so is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.cg_last_error.argtypes = []
+    lib.cg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != CG_OK:
+        msg = load().cg_last_error()
+        raise CygridError(status, msg.decode() if msg else "")
+    return status
+
+
+def _call(name):
+    def f(*args):
+        return check(getattr(load(), name)(*args))
+    f.__name__ = name
+    return f
+
+
+cg_grid_create = _call("cg_grid_create")
+cg_set_kernel = _call("cg_set_kernel")
+cg_grid_add = _call("cg_grid_add")
+cg_grid_finalize = _call("cg_grid_finalize")
+cg_grid_oneshot = _call("cg_grid_oneshot")
+cg_grid_reset = _call("cg_grid_reset")
+cg_grid_destroy = _call("cg_grid_destroy")
+cg_set_stream = _call("cg_set_stream")
+cg_set_path = _call("cg_set_path")
+cg_sync = _call("cg_sync")
+cg_get_info = _call("cg_get_info")
+cg_ang2pix_ring = _call("cg_ang2pix_ring")
+cg_grid_export_index = _call("cg_grid_export_index")
+cg_set_timing = _call("cg_set_timing")
+cg_read_timing = _call("cg_read_timing")
+
+
+def cg_last_error() -> str:
+    return load().cg_last_error().decode()

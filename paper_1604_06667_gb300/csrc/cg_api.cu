@@ -1,0 +1,429 @@
+// cg_api.cu -- the C ABI (include/cygrid_gb300.h): argument checks, the
+// planner (nside rule, kernel constants) and the ordering of the kernels on
+// the handle's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "cg_common.cuh"
+#include "cg_internal.h"
+
+using namespace cg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cg_status fail(cg_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+cg_status fail(cg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+cg_status cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(CG_ENOMEM, "%s: device allocation failed", where);
+  return fail(CG_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CG_CUDA(call, where)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+// ---- stage timing -------------------------------------------------------
+cudaEvent_t tmark(cg_grid* g) {
+  if (!g->timing) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (!g->ev_pool.empty()) {
+    e = g->ev_pool.back();
+    g->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(e, g->stream);
+  return e;
+}
+
+void tstage(cg_grid* g, int stage, cudaEvent_t a, cudaEvent_t b) {
+  if (a && b) g->timing_recs.push_back(cg_grid::TimingRec{stage, a, b});
+}
+
+void release_events(cg_grid* g) {
+  for (auto& r : g->timing_recs) {
+    g->ev_pool.push_back(r.a);
+    g->ev_pool.push_back(r.b);
+  }
+  g->timing_recs.clear();
+}
+
+// Read and clear the device error word (synchronises the stream).
+cg_status check_device(cg_grid* g, const char* where) {
+  unsigned h = 0;
+  CG_CUDA(cudaMemcpyAsync(&h, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream),
+          where);
+  CG_CUDA(cudaStreamSynchronize(g->stream), where);
+  if (h) {
+    CG_CUDA(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), g->stream), where);
+    CG_CUDA(cudaStreamSynchronize(g->stream), where);
+  }
+  if (h & ERR_BAD_TARGET)
+    return fail(CG_EINVAL, "%s: target coordinates must be finite with |lat| <= 90", where);
+  if (h & ERR_BAD_SAMPLE)
+    return fail(CG_EINVAL,
+                "%s: sample coordinates must be finite with |lat| <= 90 and weights finite "
+                "and >= 0 (offending samples were skipped)",
+                where);
+  if (h & ERR_TIMEOUT) return fail(CG_ETIMEOUT, "%s: a bounded device wait gave up", where);
+  if (h) return fail(CG_EDEVICE, "%s: device error word 0x%x", where, h);
+  return CG_OK;
+}
+
+void free_all(cg_grid* g) {
+  cudaStream_t s = g->stream;
+  dfree(g->tgt_perm, s);
+  dfree(g->tile_chi, s);
+  dfree(g->tile_clo, s);
+  dfree(g->tile_c64, s);
+  dfree(g->tgt_a, s);
+  dfree(g->tgt_e, s);
+  dfree(g->tgt_n, s);
+  dfree(g->tgt_f1, s);
+  dfree(g->tgt_f2, s);
+  dfree(g->tgt_ll, s);
+  dfree(g->range_off, s);
+  dfree(g->ranges, s);
+  dfree(g->range_s, s);
+  dfree(g->key, s);
+  dfree(g->val, s);
+  if (g->sw.keys_alt) cudaFreeAsync(g->sw.keys_alt, s);
+  g->sw.keys_alt = nullptr;
+  dfree(g->sw.vals_alt, s);
+  dfree(g->sw.hist, s);
+  dfree(g->sw.totals, s);
+  dfree(g->s_hi, s);
+  dfree(g->s_lo, s);
+  dfree(g->ring_off, s);
+  dfree(g->acc_num, s);
+  dfree(g->acc_w, s);
+  dfree(g->d_err, s);
+  dfree(g->d_pairs, s);
+  release_events(g);
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  g->ev_pool.clear();
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+cg_status zero_acc(cg_grid* g) {
+  const int64_t slots = g->n_tiles * kTile;
+  CG_CUDA(cudaMemsetAsync(g->acc_num, 0, sizeof(float) * (size_t)slots * g->C, g->stream),
+          "reset");
+  CG_CUDA(cudaMemsetAsync(g->acc_w, 0, sizeof(float2) * (size_t)slots, g->stream), "reset");
+  CG_CUDA(cudaMemsetAsync(g->d_pairs, 0, sizeof(unsigned long long), g->stream), "reset");
+  g->acc_empty = true;
+  g->total_n = 0;
+  return CG_OK;
+}
+
+cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* data,
+                 int32_t dtype, const float* weights, int64_t n, const char* where) {
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (dtype != CG_F32 && dtype != CG_BF16)
+    return fail(CG_EINVAL, "%s: data_dtype must be CG_F32 or CG_BF16", where);
+  if (n < 0 || n > 0x7fffffffLL) return fail(CG_EINVAL, "%s: n_samples out of range", where);
+  if (n == 0) return CG_OK;
+  if (!lon || !lat || !data) return fail(CG_EINVAL, "%s: null coordinate or data pointer", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  cudaEvent_t t0 = tmark(g);
+  CG_CUDA(samples_keys(g, lon, lat, n), where);
+  cudaEvent_t t1 = tmark(g);
+  CG_CUDA(samples_sort(g, n), where);
+  cudaEvent_t t2 = tmark(g);
+  CG_CUDA(samples_prepare(g, lon, lat, weights, n), where);
+  cudaEvent_t t3 = tmark(g);
+  CG_CUDA(grid_tiles_f32(g, data, dtype, lon, lat), where);
+  cudaEvent_t t4 = tmark(g);
+  tstage(g, 0, t0, t1);
+  tstage(g, 1, t1, t2);
+  tstage(g, 2, t2, t3);
+  tstage(g, 3, t3, t4);
+  g->last_path = CG_PATH_FP32;
+  g->acc_empty = false;
+  g->total_n += n;
+  return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cg_last_error(void) { return g_last_error.c_str(); }
+
+cg_status cg_grid_create(cg_grid** out, const double* lon_deg, const double* lat_deg,
+                         int64_t n_targets, int32_t n_channels, void* stream) {
+  g_last_error.clear();
+  if (!out) return fail(CG_EINVAL, "cg_grid_create: out is null");
+  *out = nullptr;
+  if (!lon_deg || !lat_deg) return fail(CG_EINVAL, "cg_grid_create: null target coordinates");
+  if (n_targets < 1 || n_targets > 0x7fffffffLL)
+    return fail(CG_EINVAL, "cg_grid_create: n_targets must be in [1, 2^31-1]");
+  if (n_channels < 1 || n_channels > 65536)
+    return fail(CG_EINVAL, "cg_grid_create: n_channels must be in [1, 65536]");
+  cg_grid* g = new (std::nothrow) cg_grid();
+  if (!g) return fail(CG_ENOMEM, "cg_grid_create: host allocation failed");
+  g->stream = static_cast<cudaStream_t>(stream);
+  g->P = n_targets;
+  g->C = n_channels;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = dalloc(&g->d_err, 1, g->stream);
+  if (e == cudaSuccess) e = dalloc(&g->d_pairs, 1, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), g->stream);
+  if (e == cudaSuccess) e = targets_build(g, lon_deg, lat_deg);
+  const int64_t slots = g->n_tiles * kTile;
+  if (e == cudaSuccess) e = dalloc(&g->acc_num, (size_t)slots * g->C, g->stream);
+  if (e == cudaSuccess) e = dalloc(&g->acc_w, (size_t)slots, g->stream);
+  if (e != cudaSuccess) {
+    cg_status st = cuda_fail(e, "cg_grid_create");
+    free_all(g);
+    cudaStreamSynchronize(g->stream);
+    delete g;
+    return st;
+  }
+  cg_status st = zero_acc(g);
+  if (st == CG_OK) st = check_device(g, "cg_grid_create");
+  if (st != CG_OK) {
+    free_all(g);
+    cudaStreamSynchronize(g->stream);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return CG_OK;
+}
+
+cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, int32_t n_params,
+                        double support_deg, int32_t nside, double hpx_maxres_deg) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_set_kernel: null handle");
+  if (!params) return fail(CG_EINVAL, "cg_set_kernel: params is null");
+  double sig1 = 0, sig2 = 0, pa = 0;
+  if (kernel_type == CG_GAUSS1D) {
+    if (n_params < 1 || !finite_pos(params[0]))
+      return fail(CG_EINVAL, "cg_set_kernel: gauss1d needs params = {sigma > 0}");
+    sig1 = sig2 = params[0];
+  } else if (kernel_type == CG_GAUSS2D) {
+    if (n_params < 3 || !finite_pos(params[0]) || !finite_pos(params[1]) ||
+        !std::isfinite(params[2]))
+      return fail(CG_EINVAL,
+                  "cg_set_kernel: gauss2d needs params = {sigma_maj > 0, sigma_min > 0, PA}");
+    sig1 = params[0];
+    sig2 = params[1];
+    pa = params[2];
+  } else {
+    return fail(CG_EINVAL, "cg_set_kernel: unknown kernel type %d", kernel_type);
+  }
+  if (!finite_pos(support_deg) || support_deg > 180.0)
+    return fail(CG_EINVAL, "cg_set_kernel: support must be in (0, 180] degrees");
+  int ns = nside;
+  if (ns == 0) {
+    if (!finite_pos(hpx_maxres_deg))
+      return fail(CG_EINVAL, "cg_set_kernel: hpx_maxres must be > 0 when nside = 0");
+    // Sect. 3.5: hpx-max-resolution ~ sigma/2; smallest power of two nside
+    // with pixel size sqrt(pi/3)/nside <= hpx_maxres
+    const double target = hpx_maxres_deg * kDeg2Rad;
+    ns = 1;
+    while (ns < 8192 && std::sqrt(kPi / 3.0) / ns > target) ns *= 2;
+  }
+  if (ns < 1 || ns > 8192) return fail(CG_EINVAL, "cg_set_kernel: nside must be in [1, 8192]");
+  CG_CUDA(cudaSetDevice(g->device), "cg_set_kernel");
+  g->kernel_type = kernel_type;
+  g->kparams[0] = params[0];
+  g->kparams[1] = (kernel_type == CG_GAUSS2D) ? params[1] : 0.0;
+  g->kparams[2] = (kernel_type == CG_GAUSS2D) ? params[2] : 0.0;
+  g->support_deg = support_deg;
+  g->nside = ns;
+  KernelDev kd{};
+  kd.type = kernel_type;
+  const double log2e = 1.4426950408889634;
+  const double s1 = sig1 * kDeg2Rad, s2 = sig2 * kDeg2Rad;
+  kd.k1 = (float)(-log2e / (2.0 * s1 * s1));
+  kd.k2 = (float)(-log2e / (2.0 * s2 * s2));
+  const double r = support_deg * kDeg2Rad;
+  const double chord = 2.0 * std::sin(0.5 * std::fmin(r, kPi));
+  kd.r_rad = r;
+  kd.c2_cut = (float)(chord * chord);
+  kd.c2_in = (float)(chord * chord * (1.0 - 1e-5));
+  kd.c2_out = (float)(chord * chord * (1.0 + 1e-5));
+  kd.big_support = chord > 0.1 ? 1 : 0;
+  g->kdev = kd;
+  if (kernel_type == CG_GAUSS2D) CG_CUDA(targets_set_axes(g, pa), "cg_set_kernel");
+  CG_CUDA(tiles_query(g), "cg_set_kernel");
+  cg_status st = zero_acc(g);
+  if (st != CG_OK) return st;
+  g->kernel_set = true;
+  return check_device(g, "cg_set_kernel");
+}
+
+cg_status cg_grid_add(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                      const void* data, int32_t data_dtype, const float* weights,
+                      int64_t n_samples) {
+  g_last_error.clear();
+  return do_add(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, "cg_grid_add");
+}
+
+cg_status cg_grid_finalize(cg_grid* g, float* out, int32_t layout_channel_major,
+                           float* out_weights) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_grid_finalize: null handle");
+  if (!out) return fail(CG_EINVAL, "cg_grid_finalize: out is null");
+  CG_CUDA(cudaSetDevice(g->device), "cg_grid_finalize");
+  cudaEvent_t t0 = tmark(g);
+  CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_finalize");
+  tstage(g, 4, t0, tmark(g));
+  return check_device(g, "cg_grid_finalize");
+}
+
+cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                          const void* data, int32_t data_dtype, const float* weights,
+                          int64_t n_samples, float* out, int32_t layout_channel_major,
+                          float* out_weights) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_grid_oneshot: null handle");
+  if (!out) return fail(CG_EINVAL, "cg_grid_oneshot: out is null");
+  if (!g->kernel_set) return fail(CG_ESTATE, "cg_grid_oneshot: call cg_set_kernel first");
+  CG_CUDA(cudaSetDevice(g->device), "cg_grid_oneshot");
+  cg_status st = zero_acc(g);
+  if (st != CG_OK) return st;
+  st = do_add(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, "cg_grid_oneshot");
+  if (st != CG_OK) return st;
+  cudaEvent_t t0 = tmark(g);
+  CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_oneshot");
+  tstage(g, 4, t0, tmark(g));
+  return CG_OK;
+}
+
+cg_status cg_grid_reset(cg_grid* g) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_grid_reset: null handle");
+  CG_CUDA(cudaSetDevice(g->device), "cg_grid_reset");
+  return zero_acc(g);
+}
+
+cg_status cg_grid_destroy(cg_grid* g) {
+  g_last_error.clear();
+  if (!g) return CG_OK;
+  cudaSetDevice(g->device);
+  free_all(g);
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  delete g;
+  if (e != cudaSuccess) return cuda_fail(e, "cg_grid_destroy");
+  return CG_OK;
+}
+
+cg_status cg_set_stream(cg_grid* g, void* stream) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_set_stream: null handle");
+  // order the new stream after all work already enqueued on the old one
+  CG_CUDA(cudaStreamSynchronize(g->stream), "cg_set_stream");
+  g->stream = static_cast<cudaStream_t>(stream);
+  return CG_OK;
+}
+
+cg_status cg_set_path(cg_grid* g, int32_t path) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_set_path: null handle");
+  if (path < CG_PATH_AUTO || path > CG_PATH_TC) return fail(CG_EINVAL, "cg_set_path: bad path");
+  g->path = path;
+  return CG_OK;
+}
+
+cg_status cg_sync(cg_grid* g) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_sync: null handle");
+  CG_CUDA(cudaSetDevice(g->device), "cg_sync");
+  return check_device(g, "cg_sync");
+}
+
+cg_status cg_get_info(cg_grid* g, cg_info* info) {
+  g_last_error.clear();
+  if (!g || !info) return fail(CG_EINVAL, "cg_get_info: null argument");
+  info->n_targets = g->P;
+  info->n_channels = g->C;
+  info->nside = g->nside;
+  info->n_tiles = g->n_tiles;
+  info->tile_size = kTile;
+  info->path = g->last_path;
+  info->n_ranges = g->n_ranges;
+  info->n_samples_total = g->total_n;
+  info->n_launches = g->n_launches;
+  unsigned long long pairs = 0;
+  CG_CUDA(cudaSetDevice(g->device), "cg_get_info");
+  CG_CUDA(cudaMemcpyAsync(&pairs, g->d_pairs, sizeof pairs, cudaMemcpyDeviceToHost, g->stream),
+          "cg_get_info");
+  CG_CUDA(cudaStreamSynchronize(g->stream), "cg_get_info");
+  info->n_pairs = (int64_t)pairs;
+  return CG_OK;
+}
+
+cg_status cg_set_timing(cg_grid* g, int32_t enable) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_set_timing: null handle");
+  g->timing = enable != 0;
+  return CG_OK;
+}
+
+cg_status cg_read_timing(cg_grid* g, double* ms, int64_t* n_grid_launches) {
+  g_last_error.clear();
+  if (!g || !ms) return fail(CG_EINVAL, "cg_read_timing: null argument");
+  CG_CUDA(cudaSetDevice(g->device), "cg_read_timing");
+  CG_CUDA(cudaStreamSynchronize(g->stream), "cg_read_timing");
+  for (int i = 0; i < CG_N_STAGES; ++i) ms[i] = 0.0;
+  int64_t ng = 0;
+  for (auto& r : g->timing_recs) {
+    float t = 0.f;
+    CG_CUDA(cudaEventElapsedTime(&t, r.a, r.b), "cg_read_timing");
+    if (r.stage >= 0 && r.stage < CG_N_STAGES) ms[r.stage] += t;
+    if (r.stage == 3) ++ng;
+  }
+  if (n_grid_launches) *n_grid_launches = ng;
+  release_events(g);
+  return CG_OK;
+}
+
+cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* lat_deg, int64_t n,
+                          int64_t* pix, void* stream) {
+  g_last_error.clear();
+  if (nside < 1 || nside > (1 << 20)) return fail(CG_EINVAL, "cg_ang2pix_ring: bad nside");
+  if (n < 0) return fail(CG_EINVAL, "cg_ang2pix_ring: n < 0");
+  if (n > 0 && (!lon_deg || !lat_deg || !pix))
+    return fail(CG_EINVAL, "cg_ang2pix_ring: null pointer");
+  CG_CUDA(ang2pix_export(nside, lon_deg, lat_deg, n, pix, static_cast<cudaStream_t>(stream)),
+          "cg_ang2pix_ring");
+  return CG_OK;
+}
+
+cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
+                               int64_t* ring_off, int64_t n) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_grid_export_index: null handle");
+  if (n != g->last_n)
+    return fail(CG_EINVAL, "cg_grid_export_index: n (%lld) != samples of the last add (%lld)",
+                (long long)n, (long long)g->last_n);
+  if (n > 0 && (!sorted_pix || !perm)) return fail(CG_EINVAL, "cg_grid_export_index: null pointer");
+  CG_CUDA(cudaSetDevice(g->device), "cg_grid_export_index");
+  CG_CUDA(export_index(g, sorted_pix, perm, ring_off, n), "cg_grid_export_index");
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// cg_internal.h -- the handle and the host-side launch wrappers shared by the
+// translation units of the library.  Not part of the public C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+// the public C ABI is the only thing the shared library exports
+#pragma GCC visibility push(default)
+#include "../../include/cygrid_gb300.h"
+#pragma GCC visibility pop
+
+namespace cg {
+
+// Tile size: targets grouped per CTA.
+constexpr int kTile = 64;
+// Candidate samples staged per chunk.
+constexpr int kChunk = 32;
+
+struct Range {            // one contiguous pixel interval of one ring
+  int32_t pix_lo;         // first pixel (inclusive)
+  int32_t pix_hi;         // last pixel (inclusive)
+  int32_t ring;           // ring number 1 .. 4ns-1
+  int32_t pad;
+};
+
+struct KernelDev {        // kernel constants used by the gridder
+  int type;               // CG_GAUSS1D / CG_GAUSS2D
+  float k1, k2;           // -log2(e) / (2 sigma^2) [rad^-2] (gauss2d: major, minor)
+  float c2_in, c2_out;    // chord^2 below c2_in: inside; above c2_out: outside
+  float c2_cut;           // chord^2 of the support radius
+  double r_rad;           // support radius (FP64 guard-band decision)
+  int big_support;        // 1 if the chord series for d^2 is not accurate enough
+};
+
+struct SortWork {         // radix-sort scratch
+  void* keys_alt = nullptr;
+  uint32_t* vals_alt = nullptr;
+  uint32_t* hist = nullptr;     // [256 * nblk]
+  uint32_t* totals = nullptr;   // [256]
+  size_t cap_n = 0, cap_hist = 0, key_bytes = 0;
+};
+
+}  // namespace cg
+
+struct cg_grid {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t P = 0;
+  int32_t C = 0;
+  int32_t path = CG_PATH_AUTO;
+  int32_t last_path = CG_PATH_FP32;
+
+  // targets, in tile order (slot = tile * kTile + lane; empty slots marked)
+  int64_t n_tiles = 0;
+  uint32_t* tgt_perm = nullptr;   // [n_tiles*kTile] user index or 0xffffffff
+  float4* tile_chi = nullptr;     // [n_tiles] centre hi (xyz), w = radius (rad)
+  float4* tile_clo = nullptr;     // [n_tiles] centre lo (xyz)
+  double4* tile_c64 = nullptr;    // [n_tiles] FP64 centre (xyz), w = radius
+  float4* tgt_a = nullptr;        // [slots] u_t - centre (FP32)
+  float4* tgt_e = nullptr;        // [slots] local east unit vector
+  float4* tgt_n = nullptr;        // [slots] local north unit vector
+  float4* tgt_f1 = nullptr;       // [slots] major-axis direction (set_kernel)
+  float4* tgt_f2 = nullptr;       // [slots] minor-axis direction (set_kernel)
+  double2* tgt_ll = nullptr;      // [slots] lon/lat degrees (FP64)
+
+  // kernel and candidate query
+  bool kernel_set = false;
+  int32_t kernel_type = 0;
+  double kparams[3] = {0, 0, 0};
+  double support_deg = 0;
+  int32_t nside = 0;
+  cg::KernelDev kdev{};
+  int64_t n_ranges = 0;
+  int64_t* range_off = nullptr;   // [n_tiles + 1]
+  cg::Range* ranges = nullptr;    // [n_ranges]
+
+  // per-add sample workspace
+  size_t cap_n = 0;
+  uint32_t* key = nullptr;        // [cap_n] RING index of each sample
+  uint32_t* val = nullptr;        // [cap_n] sample index
+  cg::SortWork sw;
+  uint32_t* sorted_key = nullptr; // points at key or sw.keys_alt after the sort
+  uint32_t* sorted_val = nullptr;
+  float4* s_hi = nullptr;         // [cap_n] sorted samples: unit vector hi, w = omega
+  float4* s_lo = nullptr;         // [cap_n] unit vector lo
+  int32_t* ring_off = nullptr;    // [4*nside + 1]
+  int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi)
+  int64_t last_n = 0;
+  int64_t total_n = 0;
+
+  // accumulators (tile order)
+  float* acc_num = nullptr;       // [slots][C]
+  float2* acc_w = nullptr;        // [slots] double-float weight sum
+  bool acc_empty = true;
+
+  unsigned* d_err = nullptr;      // device error word
+  unsigned long long* d_pairs = nullptr;  // pairs with d <= r since the last reset
+  int64_t n_launches = 0;         // kernels launched by this handle
+
+  // optional stage timing (CUDA events on the handle's stream)
+  struct TimingRec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<TimingRec> timing_recs;
+};
+
+namespace cg {
+
+// k_sort.cu -- stable LSD radix sort of (key, value) pairs.
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                           SortWork& w, cudaStream_t s, uint32_t** out_keys,
+                           uint32_t** out_vals);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                           SortWork& w, cudaStream_t s, uint64_t** out_keys,
+                           uint32_t** out_vals);
+
+// k_targets.cu -- target geometry and tiling.
+cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat);
+cudaError_t targets_set_axes(cg_grid* g, double pa_deg);
+
+// k_healpix.cu -- ang2pix, ring offsets, tile disc queries, sample ranges.
+cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int64_t n,
+                           int64_t* pix, cudaStream_t s);
+cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, int64_t n);
+cudaError_t samples_sort(cg_grid* g, int64_t n);
+cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
+                            const float* weights, int64_t n);
+cudaError_t tiles_query(cg_grid* g);
+cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t* ring_off,
+                         int64_t n);
+
+// k_grid.cu -- the tile gridder (FP32 CUDA-core form).
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
+                           const double* lat);
+// k_finalize.cu -- normalisation and output layout.
+cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w);
+
+// device allocation helper (stream ordered); returns cudaErrorMemoryAllocation on failure
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace cg

@@ -1,0 +1,397 @@
+// k_grid.cu -- tile gridder, FP32 CUDA-core form (paper Eq. 1-2).
+//
+// One CTA owns one tile of kTile targets, so no two CTAs ever write the same
+// output cell: the race-free ownership of target pixels of the paper's lookup
+// scheme (Sect. 2.2, "the program writes into different map and weight-map
+// cells in each thread"), with a CTA in place of a CPU thread.
+//
+// The CTA walks the tile's candidate samples -- the sample ranges that the
+// tile's disc query selected -- in chunks of kChunk:
+//   stage    candidate unit vectors (double-float), sample weight, data rows
+//            into shared memory;
+//   phase A  weights w[k][p] for every (candidate, target) pair: chord between
+//            tile-relative FP32 vectors, exact cut d <= r (FP64 recomputation
+//            inside a narrow guard band around r), Gaussian via ex2;
+//            per-target weight sums W_p with Neumaier compensation;
+//   phase B  register-blocked accumulation acc[p][c] += w[k][p] * D[k][c],
+//            skipping candidates whose weights for the thread's targets are 0.
+// The epilogue adds acc into the numerator and W into the weight map (tile
+// order; cg_grid_finalize applies Eq. 3 and the user layout).
+#include <cuda_bf16.h>
+
+#include "cg_common.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+namespace {
+
+constexpr int kRangeBatch = 256;
+
+struct GridArgs {
+  const float4* tile_chi;
+  const float4* tile_clo;
+  const float4* tgt_a;
+  const float4* tgt_f1;
+  const float4* tgt_f2;
+  const double2* tgt_ll;
+  const uint32_t* tgt_perm;
+  const int64_t* range_off;
+  const int2* range_s;
+  const float4* s_hi;
+  const float4* s_lo;
+  const uint32_t* perm;
+  const double* lon;
+  const double* lat;
+  const void* data;
+  int C;
+  int vec4;  // data rows are 16-byte (f32) / 8-byte (bf16) aligned in groups of 4
+  KernelDev kd;
+  float* acc_num;
+  float2* acc_w;
+  int accumulate;
+  unsigned long long* pairs;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Great-circle distance by the Haversine formula in FP64 (guard band only).
+__device__ __noinline__ double haversine_f64(double l1, double b1, double l2, double b2) {
+  const double p1 = b1 * kDeg2Rad, p2 = b2 * kDeg2Rad;
+  const double dl = (l2 - l1) * kDeg2Rad;
+  const double sdp = sin(0.5 * (p2 - p1));
+  const double sdl = sin(0.5 * dl);
+  double h = sdp * sdp + cos(p1) * cos(p2) * sdl * sdl;
+  h = fmin(h, 1.0);
+  return 2.0 * asin(sqrt(h));
+}
+
+template <typename DT>
+__device__ __forceinline__ float load_elem(const DT* p);
+template <>
+__device__ __forceinline__ float load_elem<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_elem<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+template <typename DT>
+__device__ __forceinline__ float4 load_vec4(const DT* p);
+template <>
+__device__ __forceinline__ float4 load_vec4<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <>
+__device__ __forceinline__ float4 load_vec4<__nv_bfloat16>(const __nv_bfloat16* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  float4 r;
+  r.x = __uint_as_float(u.x << 16);
+  r.y = __uint_as_float(u.x & 0xffff0000u);
+  r.z = __uint_as_float(u.y << 16);
+  r.w = __uint_as_float(u.y & 0xffff0000u);
+  return r;
+}
+
+// PB targets x CB channels per thread in phase B; NCG channel groups.
+template <int PB, int CB, int NCG, typename DT>
+__global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
+  constexpr int NTH = (kTile / PB) * NCG;
+  constexpr int CPAD = CB * NCG;
+  constexpr int K = kChunk;
+  constexpr int STEP = NTH / kTile;
+  static_assert(NTH % kTile == 0, "threads must cover the tile");
+  static_assert(CB % 4 == 0, "channel blocks are float4 wide");
+
+  __shared__ float4 sh_hi[K];
+  __shared__ float4 sh_lo[K];
+  __shared__ uint32_t sh_idx[K];
+  __shared__ __align__(16) float w_s[K][kTile];
+  __shared__ __align__(16) float d_s[K][CPAD];
+  __shared__ int2 rg[kRangeBatch];
+  __shared__ int rg_pre[kRangeBatch + 1];
+  __shared__ float2 wred[NTH];
+
+  const int tid = threadIdx.x;
+  const int64_t tile = blockIdx.x;
+  const int c_base = blockIdx.y * CPAD;
+
+  // phase-A identity: one target, every STEP-th candidate
+  const int p = tid % kTile;
+  const int kk0 = tid / kTile;
+  const int64_t slot = tile * kTile + p;
+  const float4 at = a.tgt_a[slot];
+  float4 f1 = make_float4(0, 0, 0, 0), f2 = f1;
+  if (a.kd.type == CG_GAUSS2D) {
+    f1 = a.tgt_f1[slot];
+    f2 = a.tgt_f2[slot];
+  }
+  const float4 chi = a.tile_chi[tile];
+  const float4 clo = a.tile_clo[tile];
+  float ws = 0.f, wc = 0.f;  // Neumaier sum of weights
+  unsigned npair = 0;        // pairs inside the support
+
+  // phase-B identity
+  const int pg = tid / NCG;
+  const int cg = tid % NCG;
+  float acc[PB][CB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i)
+#pragma unroll
+    for (int j = 0; j < CB; ++j) acc[i][j] = 0.f;
+
+  const DT* data = static_cast<const DT*>(a.data);
+  const int C = a.C;
+  const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
+
+  for (int64_t rb = r0; rb < r1; rb += kRangeBatch) {
+    const int nr = (int)((r1 - rb) < kRangeBatch ? (r1 - rb) : kRangeBatch);
+    __syncthreads();
+    if (tid < 32) {
+      // warp 0: load this batch of ranges and prefix-sum their lengths
+      int carry = 0;
+      for (int b = 0; b < nr; b += 32) {
+        const int q = b + tid;
+        int len = 0;
+        if (q < nr) {
+          const int2 r = a.range_s[rb + q];
+          rg[q] = r;
+          len = r.y - r.x;
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (tid >= o) incl += y;
+        }
+        if (q < nr) rg_pre[q] = carry + incl - len;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (tid == 0) rg_pre[nr] = carry;
+    }
+    __syncthreads();
+    const int total = rg_pre[nr];
+
+    for (int v0 = 0; v0 < total; v0 += K) {
+      // ---- stage candidates ----
+      if (tid < K) {
+        const int v = v0 + tid;
+        if (v < total) {
+          int lo = 0, hi = nr - 1;  // last range with rg_pre <= v
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
+          }
+          const int64_t s = rg[lo].x + (v - rg_pre[lo]);
+          sh_hi[tid] = a.s_hi[s];
+          sh_lo[tid] = a.s_lo[s];
+          sh_idx[tid] = a.perm[s];
+        } else {
+          sh_hi[tid] = make_float4(4.f, 4.f, 4.f, 0.f);
+          sh_lo[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sh_idx[tid] = 0xffffffffu;
+        }
+      }
+      __syncthreads();
+      if (a.vec4) {
+        for (int e = tid; e < K * (CPAD / 4); e += NTH) {
+          const int k = e / (CPAD / 4);
+          const int c = (e % (CPAD / 4)) * 4;
+          const uint32_t idx = sh_idx[k];
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (idx != 0xffffffffu && c_base + c < C)
+            v = load_vec4<DT>(data + (size_t)idx * C + c_base + c);
+          *reinterpret_cast<float4*>(&d_s[k][c]) = v;
+        }
+      } else {
+        for (int e = tid; e < K * CPAD; e += NTH) {
+          const int k = e / CPAD;
+          const int c = e % CPAD;
+          const uint32_t idx = sh_idx[k];
+          float v = 0.f;
+          if (idx != 0xffffffffu && c_base + c < C) v = load_elem<DT>(data + (size_t)idx * C + c_base + c);
+          d_s[k][c] = v;
+        }
+      }
+
+      // ---- phase A: weights ----
+#pragma unroll 2
+      for (int k = kk0; k < K; k += STEP) {
+        const float4 sh = sh_hi[k];
+        const float4 sl = sh_lo[k];
+        const float bx = df_diff(sh.x, sl.x, chi.x, clo.x);
+        const float by = df_diff(sh.y, sl.y, chi.y, clo.y);
+        const float bz = df_diff(sh.z, sl.z, chi.z, clo.z);
+        const float dx = at.x - bx, dy = at.y - by, dz = at.z - bz;
+        const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float w = 0.f;
+        if (c2 <= a.kd.c2_out) {
+          float d2;
+          if (!a.kd.big_support) {
+            d2 = c2 * fmaf(c2, fmaf(c2, 1.f / 90.f, 1.f / 12.f), 1.f);
+          } else {
+            const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+            d2 = d * d;
+          }
+          float ex;
+          if (a.kd.type == CG_GAUSS1D) {
+            ex = a.kd.k1 * d2;
+          } else {
+            const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+            const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+            const float s2 = fmaf(ap, ap, bp * bp);  // sin^2 d
+            const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+            ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
+          }
+          w = ex2_approx(ex) * sh.w;
+          if (c2 >= a.kd.c2_in) {
+            // guard band: decide d <= r in FP64 from the input coordinates
+            const uint32_t idx = sh_idx[k];
+            const double2 tl = a.tgt_ll[slot];
+            const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+            if (!(d <= a.kd.r_rad)) w = -1.f;
+          }
+          if (w >= 0.f) ++npair; else w = 0.f;
+        }
+        w_s[k][p] = w;
+        // Neumaier (two-sum) accumulation of the weight map
+        const float t = ws + w;
+        const float bp2 = t - ws;
+        wc += (ws - (t - bp2)) + (w - bp2);
+        ws = t;
+      }
+      __syncthreads();
+
+      // ---- phase B: channel accumulation ----
+#pragma unroll 4
+      for (int k = 0; k < K; ++k) {
+        float wv[PB];
+        if constexpr (PB == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(&w_s[k][pg * 4]);
+          wv[0] = q.x; wv[1] = q.y; wv[2] = q.z; wv[3] = q.w;
+        } else if constexpr (PB == 2) {
+          const float2 q = *reinterpret_cast<const float2*>(&w_s[k][pg * 2]);
+          wv[0] = q.x; wv[1] = q.y;
+        } else {
+#pragma unroll
+          for (int i = 0; i < PB; ++i) wv[i] = w_s[k][pg * PB + i];
+        }
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < PB; ++i) any |= (wv[i] != 0.f);
+        if (!any) continue;
+#pragma unroll
+        for (int q = 0; q < CB / 4; ++q) {
+          const float4 dv = *reinterpret_cast<const float4*>(&d_s[k][4 * cg + 4 * NCG * q]);
+#pragma unroll
+          for (int i = 0; i < PB; ++i) {
+            acc[i][4 * q + 0] = fmaf(wv[i], dv.x, acc[i][4 * q + 0]);
+            acc[i][4 * q + 1] = fmaf(wv[i], dv.y, acc[i][4 * q + 1]);
+            acc[i][4 * q + 2] = fmaf(wv[i], dv.z, acc[i][4 * q + 2]);
+            acc[i][4 * q + 3] = fmaf(wv[i], dv.w, acc[i][4 * q + 3]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- epilogue: numerator ----
+#pragma unroll
+  for (int i = 0; i < PB; ++i) {
+    const int64_t sl = tile * kTile + pg * PB + i;
+    if (a.tgt_perm[sl] == 0xffffffffu) continue;
+    float* dst = a.acc_num + (size_t)sl * C;
+#pragma unroll
+    for (int q = 0; q < CB / 4; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c_base + 4 * cg + 4 * NCG * q + j;
+        if (c < C) dst[c] = a.accumulate ? dst[c] + acc[i][4 * q + j] : acc[i][4 * q + j];
+      }
+  }
+  // ---- epilogue: weight map and pair count (first channel slab only) ----
+  if (blockIdx.y != 0) return;
+  wred[tid] = make_float2(ws, wc);
+  {
+    unsigned c = npair;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((tid & 31) == 0 && c) atomicAdd(a.pairs, (unsigned long long)c);
+  }
+  __syncthreads();
+  if (kk0 == 0 && a.tgt_perm[slot] != 0xffffffffu) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int q = 0; q < STEP; ++q) {
+      const float2 v = wred[q * kTile + p];
+      const float t = s + v.x;
+      const float bp2 = t - s;
+      c += (s - (t - bp2)) + (v.x - bp2) + v.y;
+      s = t;
+    }
+    float2 old = a.accumulate ? a.acc_w[slot] : make_float2(0.f, 0.f);
+    const float t = old.x + s;
+    const float bp2 = t - old.x;
+    const float err = (old.x - (t - bp2)) + (s - bp2);
+    a.acc_w[slot] = make_float2(t, old.y + c + err);
+  }
+}
+
+template <int PB, int CB, int NCG>
+cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s) {
+  constexpr int NTH = (kTile / PB) * NCG;
+  constexpr int CPAD = CB * NCG;
+  const dim3 grid((unsigned)n_tiles, (unsigned)((a.C + CPAD - 1) / CPAD));
+  if (n_tiles == 0) return cudaSuccess;
+  if (dtype == CG_BF16)
+    k_grid_f32<PB, CB, NCG, __nv_bfloat16><<<grid, NTH, 0, s>>>(a);
+  else
+    k_grid_f32<PB, CB, NCG, float><<<grid, NTH, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
+                           const double* lat) {
+  GridArgs a;
+  a.tile_chi = g->tile_chi;
+  a.tile_clo = g->tile_clo;
+  a.tgt_a = g->tgt_a;
+  a.tgt_f1 = g->tgt_f1;
+  a.tgt_f2 = g->tgt_f2;
+  a.tgt_ll = g->tgt_ll;
+  a.tgt_perm = g->tgt_perm;
+  a.range_off = g->range_off;
+  a.range_s = g->range_s;
+  a.s_hi = g->s_hi;
+  a.s_lo = g->s_lo;
+  a.perm = g->sorted_val;
+  a.lon = lon;
+  a.lat = lat;
+  a.data = data;
+  a.C = g->C;
+  const size_t esz = (dtype == CG_BF16) ? 2 : 4;
+  a.vec4 = (g->C % 4 == 0) && ((reinterpret_cast<uintptr_t>(data) % (4 * esz)) == 0);
+  a.kd = g->kdev;
+  a.acc_num = g->acc_num;
+  a.acc_w = g->acc_w;
+  a.accumulate = g->acc_empty ? 0 : 1;
+  a.pairs = g->d_pairs;
+  g->n_launches += 1;
+  const int C = g->C;
+  const int64_t nt = g->n_tiles;
+  cudaStream_t s = g->stream;
+  if (C <= 4) return launch<1, 4, 1>(a, nt, dtype, s);
+  if (C <= 8) return launch<1, 8, 1>(a, nt, dtype, s);
+  if (C <= 16) return launch<1, 8, 2>(a, nt, dtype, s);
+  if (C <= 32) return launch<2, 8, 4>(a, nt, dtype, s);
+  if (C <= 64) return launch<2, 16, 4>(a, nt, dtype, s);
+  if (C <= 128) return launch<4, 16, 8>(a, nt, dtype, s);
+  return launch<4, 16, 16>(a, nt, dtype, s);
+}
+
+}  // namespace cg

@@ -1,0 +1,398 @@
+// k_healpix.cu -- the HEALPix lookup of the paper (Sect. 2.2, 3.3, 3.4) on
+// the GPU, reorganised around target tiles instead of per-sample discs:
+//
+//   samples:  RING index of every sample (Sect. 2.2 step 3a), a stable sort by
+//             index (replacing the hash tables of Sect. 3.4), per-ring offsets
+//             into the sorted order, and the sorted samples' unit vectors;
+//   tiles:    one disc query per tile of targets (Sect. 2.2 step 3b, done once
+//             per tile rather than once per sample), radius = tile radius +
+//             support, as closed-form pixel intervals per ring (the per-ring
+//             treatment of Sect. 3.3);
+//   ranges:   each pixel interval becomes a contiguous range of sorted samples
+//             by two binary searches inside its ring.
+#include "cg_common.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+namespace {
+
+struct RingGeo {
+  int64_t count, first;
+  double z, phase;
+};
+
+__device__ __forceinline__ RingGeo ring_geo(int64_t ns, int64_t i) {
+  RingGeo r;
+  const double dns = (double)ns;
+  if (i < ns) {
+    r.count = 4 * i;
+    r.first = 2 * i * (i - 1);
+    r.z = 1.0 - (double)(i * i) / (3.0 * dns * dns);
+    r.phase = 0.5;
+  } else if (i <= 3 * ns) {
+    r.count = 4 * ns;
+    r.first = 2 * ns * (ns - 1) + (i - ns) * 4 * ns;
+    r.z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * dns);
+    r.phase = (((i - ns) & 1) == 0) ? 0.5 : 0.0;
+  } else {
+    const int64_t k = 4 * ns - i;
+    r.count = 4 * k;
+    r.first = 12 * ns * ns - 2 * k * (k + 1);
+    r.z = -(1.0 - (double)(k * k) / (3.0 * dns * dns));
+    r.phase = 0.5;
+  }
+  return r;
+}
+
+__device__ __forceinline__ double ring_colat(int64_t ns, int64_t i) {
+  if (i <= 0) return 0.0;
+  if (i >= 4 * ns) return kPi;
+  return acos(ring_geo(ns, i).z);
+}
+
+// Continuous ring coordinate of a direction with cos(colatitude) = z.
+__device__ __forceinline__ double ring_coord(int64_t ns, double z) {
+  const double dns = (double)ns;
+  if (fabs(z) <= 2.0 / 3.0) return dns * (2.0 - 1.5 * z);
+  if (z > 0.0) return dns * sqrt(3.0 * (1.0 - z));
+  return 4.0 * dns - dns * sqrt(3.0 * (1.0 + z));
+}
+
+// Widest longitude half-width of the disc (centre colatitude tc, radius R)
+// over the colatitude band [ta, tb]: -1 if the disc misses the band, >= pi if
+// it covers every longitude there.  The half-width at colatitude t solves
+// cos R = cos tc cos t + sin tc sin t cos(dphi); its widest point over t is
+// at cos t = cos tc / cos R (or at a band edge).
+__device__ double disc_halfwidth(double tc, double R, double ta, double tb) {
+  if (tb < tc - R || ta > tc + R) return -1.0;
+  if (ta <= 0.0 && tc <= R) return 4.0 * kPi;
+  if (tb >= kPi && tc + R >= kPi) return 4.0 * kPi;
+  const double st = sin(tc), ct = cos(tc), cr = cos(R);
+  if (st <= 0.0) return 4.0 * kPi;
+  double lo = fmax(ta, tc - R), hi = fmin(tb, tc + R);
+  lo = fmax(lo, 1e-300);
+  hi = fmin(hi, kPi - 1e-16);
+  double ts = (fabs(ct / cr) <= 1.0) ? acos(ct / cr) : lo;
+  ts = fmin(fmax(ts, lo), hi);
+  double xmin = 1e300;
+  const double cand[3] = {lo, hi, ts};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double x = (cr - ct * cos(cand[q])) / (st * sin(cand[q]));
+    xmin = fmin(xmin, x);
+  }
+  if (xmin <= -1.0) return 4.0 * kPi;
+  if (xmin > 1.0) return -1.0;
+  return acos(xmin);
+}
+
+// Pixel ranges of ring i met by the disc; writes up to 2 into out (if given).
+__device__ int ring_ranges(int64_t ns, int64_t i, double tc, double pc, double R,
+                           Range* out) {
+  const double hw = disc_halfwidth(tc, R, ring_colat(ns, i - 1), ring_colat(ns, i + 1));
+  if (hw < 0.0) return 0;
+  const RingGeo g = ring_geo(ns, i);
+  const double dphi = 2.0 * kPi / (double)g.count;
+  const double W = hw + 0.5 * dphi + 1e-12;
+  int64_t jlo = 0, jhi = g.count - 1;
+  bool full = W >= kPi;
+  if (!full) {
+    jlo = (int64_t)ceil((pc - W) / dphi - g.phase);
+    jhi = (int64_t)floor((pc + W) / dphi - g.phase);
+    if (jhi < jlo) return 0;
+    if (jhi - jlo + 1 >= g.count) full = true;
+  }
+  if (full) {
+    if (out) out[0] = Range{(int32_t)g.first, (int32_t)(g.first + g.count - 1), (int32_t)i, 0};
+    return 1;
+  }
+  int64_t a = jlo % g.count, b = jhi % g.count;
+  if (a < 0) a += g.count;
+  if (b < 0) b += g.count;
+  if (a <= b) {
+    if (out) out[0] = Range{(int32_t)(g.first + a), (int32_t)(g.first + b), (int32_t)i, 0};
+    return 1;
+  }
+  if (out) {
+    out[0] = Range{(int32_t)g.first, (int32_t)(g.first + b), (int32_t)i, 0};
+    out[1] = Range{(int32_t)(g.first + a), (int32_t)(g.first + g.count - 1), (int32_t)i, 0};
+  }
+  return 2;
+}
+
+// One warp per tile; mode 0 counts ranges, mode 1 writes them.
+__global__ void k_tile_query(const double4* __restrict__ tc64, int64_t n_tiles, int64_t ns,
+                             double r_rad, int64_t* __restrict__ counts,
+                             const int64_t* __restrict__ offs, Range* __restrict__ out,
+                             int mode) {
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= n_tiles) return;
+  const double4 c = tc64[tile];
+  const double R = c.w + r_rad;
+  const double tcol = acos(fmin(1.0, fmax(-1.0, c.z)));
+  const double pc = atan2(c.y, c.x);
+  const double tlo = fmax(0.0, tcol - R), thi = fmin(kPi, tcol + R);
+  int64_t ilo = (int64_t)floor(ring_coord(ns, cos(tlo))) - 2;
+  int64_t ihi = (int64_t)ceil(ring_coord(ns, cos(thi))) + 2;
+  ilo = ilo < 1 ? 1 : ilo;
+  ihi = ihi > 4 * ns - 1 ? 4 * ns - 1 : ihi;
+  int64_t pos = (mode == 1) ? offs[tile] : 0;
+  int64_t total = 0;
+  for (int64_t base = ilo; base <= ihi; base += 32) {
+    const int64_t i = base + lane;
+    Range rr[2];
+    const int n = (i <= ihi) ? ring_ranges(ns, i, tcol, pc, R, rr) : 0;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int sum = __shfl_sync(0xffffffffu, incl, 31);
+    if (mode == 1) {
+      for (int q = 0; q < n; ++q) out[pos + incl - n + q] = rr[q];
+      pos += sum;
+    }
+    total += sum;
+  }
+  if (mode == 0 && lane == 0) counts[tile] = total;
+}
+
+__device__ __forceinline__ bool valid_coord(double lon, double lat) {
+  return isfinite(lon) && isfinite(lat) && lat >= -90.0 && lat <= 90.0;
+}
+
+__global__ void k_ang2pix_export(int64_t ns, const double* __restrict__ lon,
+                                 const double* __restrict__ lat, int64_t n,
+                                 int64_t* __restrict__ pix) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double lo = lon[i], la = lat[i];
+  pix[i] = valid_coord(lo, la) ? ang2pix_ring_f64(ns, lo, la) : -1;
+}
+
+// Sample keys: RING index (invalid samples get npix and sort to the end).
+__global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
+                              const double* __restrict__ lat, int64_t n,
+                              uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                              unsigned* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double lo = lon[i], la = lat[i];
+  uint32_t k;
+  if (valid_coord(lo, la)) {
+    k = (uint32_t)ang2pix_ring_f64(ns, lo, la);
+  } else {
+    k = (uint32_t)(12 * ns * ns);
+    set_error(err, ERR_BAD_SAMPLE);
+  }
+  key[i] = k;
+  val[i] = (uint32_t)i;
+}
+
+// Sorted samples: unit vector as (hi, lo) float pairs, w = sample weight.
+__global__ void k_sample_gather(int64_t ns, const uint32_t* __restrict__ skey,
+                                const uint32_t* __restrict__ sval,
+                                const double* __restrict__ lon, const double* __restrict__ lat,
+                                const float* __restrict__ weights, int64_t n,
+                                float4* __restrict__ s_hi, float4* __restrict__ s_lo,
+                                unsigned* err) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t idx = sval[s];
+  if ((int64_t)skey[s] >= 12 * ns * ns) {
+    s_hi[s] = make_float4(4.f, 4.f, 4.f, 0.f);
+    s_lo[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  double sb, cb, sl, cl;
+  sincos(lat[idx] * kDeg2Rad, &sb, &cb);
+  sincos(lon[idx] * kDeg2Rad, &sl, &cl);
+  float hx, lx, hy, ly, hz, lz;
+  split_f64(cb * cl, hx, lx);
+  split_f64(cb * sl, hy, ly);
+  split_f64(sb, hz, lz);
+  float w = 1.f;
+  if (weights) {
+    w = weights[idx];
+    if (!(w >= 0.f) || !isfinite(w)) {
+      set_error(err, ERR_BAD_SAMPLE);
+      w = 0.f;
+    }
+  }
+  s_hi[s] = make_float4(hx, hy, hz, w);
+  s_lo[s] = make_float4(lx, ly, lz, 0.f);
+}
+
+// ring_off[i] = first sorted position with ring >= i, i = 0 .. 4ns.
+__global__ void k_ring_off(int64_t ns, const uint32_t* __restrict__ skey, int64_t n,
+                           int32_t* __restrict__ ring_off) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  const int64_t npix = 12 * ns * ns;
+  const int64_t end = 4 * ns;
+  auto ring = [&](int64_t q) -> int64_t {
+    const int64_t k = skey[q];
+    return (k >= npix) ? end : (int64_t)ring_of_pix(ns, k);
+  };
+  const int64_t rc = (s < n) ? ring(s) : end;
+  const int64_t rp = (s == 0) ? -1 : ring(s - 1);
+  for (int64_t i = rp + 1; i <= rc; ++i) ring_off[i] = (int32_t)s;
+}
+
+__device__ __forceinline__ int32_t lower_bound_u32(const uint32_t* __restrict__ a, int32_t lo,
+                                                   int32_t hi, uint32_t v) {
+  while (lo < hi) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_sample_ranges(const Range* __restrict__ ranges, int64_t n_ranges,
+                                const int32_t* __restrict__ ring_off,
+                                const uint32_t* __restrict__ skey, int2* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_ranges) return;
+  const Range q = ranges[r];
+  const int32_t a = ring_off[q.ring], b = ring_off[q.ring + 1];
+  int32_t lo = a, hi = a;
+  if (b > a) {
+    lo = lower_bound_u32(skey, a, b, (uint32_t)q.pix_lo);
+    hi = lower_bound_u32(skey, lo, b, (uint32_t)q.pix_hi + 1u);
+  }
+  out[r] = make_int2(lo, hi);
+}
+
+__global__ void k_export(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
+                         int64_t n, int64_t* __restrict__ pix, int64_t* __restrict__ perm) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  pix[s] = skey[s];
+  perm[s] = sval[s];
+}
+
+__global__ void k_export_ring(const int32_t* __restrict__ ro, int64_t m, int64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = ro[i];
+}
+
+int key_bits_for(int64_t ns) {
+  const uint64_t maxkey = (uint64_t)(12 * ns * ns);  // sentinel for invalid samples
+  int b = 0;
+  while (b < 32 && (maxkey >> b) != 0) ++b;
+  return b;
+}
+
+}  // namespace
+
+cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int64_t n,
+                           int64_t* pix, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ang2pix_export<<<ceil_div(n, 256), 256, 0, s>>>(nside, lon, lat, n, pix);
+  return cudaGetLastError();
+}
+
+cudaError_t tiles_query(cg_grid* g) {
+  cudaStream_t s = g->stream;
+  const int64_t nt = g->n_tiles;
+  const double r = g->support_deg * kDeg2Rad;
+  int64_t* counts = nullptr;
+  cudaError_t e;
+  dfree(g->range_off, s);
+  dfree(g->ranges, s);
+  dfree(g->range_s, s);
+  if ((e = dalloc(&counts, (size_t)nt, s)) != cudaSuccess) return e;
+  const int warps = 8;
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(g->tile_c64, nt, g->nside, r, counts,
+                                                        nullptr, nullptr, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int64_t* h = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt + 1));
+  if (!h) return cudaErrorMemoryAllocation;
+  e = cudaMemcpyAsync(h + 1, counts, sizeof(int64_t) * (size_t)nt, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { free(h); return e; }
+  h[0] = 0;
+  for (int64_t t = 0; t < nt; ++t) h[t + 1] += h[t];
+  g->n_ranges = h[nt];
+  if ((e = dalloc(&g->range_off, (size_t)nt + 1, s)) != cudaSuccess) { free(h); return e; }
+  if ((e = dalloc(&g->ranges, (size_t)g->n_ranges, s)) != cudaSuccess) { free(h); return e; }
+  if ((e = dalloc(&g->range_s, (size_t)g->n_ranges, s)) != cudaSuccess) { free(h); return e; }
+  e = cudaMemcpyAsync(g->range_off, h, sizeof(int64_t) * (size_t)(nt + 1),
+                      cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  free(h);
+  if (e != cudaSuccess) return e;
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(g->tile_c64, nt, g->nside, r, nullptr,
+                                                        g->range_off, g->ranges, 1);
+  dfree(counts, s);
+  dfree(g->ring_off, s);
+  if ((e = dalloc(&g->ring_off, (size_t)(4 * g->nside + 1), s)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
+  if (g->cap_n >= (size_t)n) return cudaSuccess;
+  cudaStream_t s = g->stream;
+  dfree(g->key, s);
+  dfree(g->val, s);
+  dfree(g->s_hi, s);
+  dfree(g->s_lo, s);
+  g->cap_n = 0;
+  cudaError_t e;
+  if ((e = dalloc(&g->key, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->val, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->s_hi, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->s_lo, (size_t)n, s)) != cudaSuccess) return e;
+  g->cap_n = (size_t)n;
+  return cudaSuccess;
+}
+
+cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, int64_t n) {
+  cudaError_t e = ensure_samples(g, n);
+  if (e != cudaSuccess) return e;
+  k_sample_keys<<<ceil_div(n, 256), 256, 0, g->stream>>>(g->nside, lon, lat, n, g->key, g->val,
+                                                         g->d_err);
+  g->n_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t samples_sort(cg_grid* g, int64_t n) {
+  const int bits = key_bits_for(g->nside);
+  g->n_launches += 3 * ((bits + 7) / 8);
+  return radix_sort_u32(g->key, g->val, n, bits, g->sw, g->stream, &g->sorted_key,
+                        &g->sorted_val);
+}
+
+cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
+                            const float* weights, int64_t n) {
+  cudaStream_t s = g->stream;
+  const int64_t ns = g->nside;
+  k_sample_gather<<<ceil_div(n, 256), 256, 0, s>>>(ns, g->sorted_key, g->sorted_val, lon, lat,
+                                                   weights, n, g->s_hi, g->s_lo, g->d_err);
+  k_ring_off<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, g->sorted_key, n, g->ring_off);
+  g->n_launches += 2;
+  if (g->n_ranges > 0) {
+    k_sample_ranges<<<ceil_div(g->n_ranges, 256), 256, 0, s>>>(g->ranges, g->n_ranges,
+                                                               g->ring_off, g->sorted_key,
+                                                               g->range_s);
+    g->n_launches += 1;
+  }
+  g->last_n = n;
+  return cudaGetLastError();
+}
+
+cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t* ring_off,
+                         int64_t n) {
+  cudaStream_t s = g->stream;
+  if (n > 0) k_export<<<ceil_div(n, 256), 256, 0, s>>>(g->sorted_key, g->sorted_val, n,
+                                                      sorted_pix, perm);
+  if (ring_off) {
+    const int64_t m = 4 * (int64_t)g->nside + 1;
+    k_export_ring<<<ceil_div(m, 256), 256, 0, s>>>(g->ring_off, m, ring_off);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,316 @@
+// k_targets.cu -- target geometry and tiling (set-up, once per handle).
+//
+// The paper grids onto the pixel centres of a WCS map or onto a list of sight
+// lines (Sect. 3.5, WcsGrid / SlGrid).  Here targets are always a list of
+// directions.  To give each CTA a compact group of targets (its "tile"), the
+// targets are split by a k-d tree over their unit vectors: every node is cut
+// along its widest axis at a multiple of kTile targets, so all leaves hold
+// exactly kTile targets (except the last) and each leaf is a compact box.
+// The tree is built level by level with one stable 64-bit radix sort per
+// level keyed by (child node, coordinate along the child's widest axis).
+// Each tile stores
+//   - its centre e_c (FP64, and as a double-float pair) and angular radius;
+//   - for every member, u_t - e_c in FP32 (accurate relative to its size);
+//   - the local east / north unit vectors (for the elliptical kernel);
+//   - the member's longitude / latitude in FP64 (guard-band recomputation).
+// FP64 is acceptable here: this runs once per target set, not per sample.
+#include "cg_common.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+namespace {
+
+__device__ __forceinline__ uint32_t orderable(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ bool valid_coord(double lon, double lat) {
+  return isfinite(lon) && isfinite(lat) && lat >= -90.0 && lat <= 90.0;
+}
+
+__device__ __forceinline__ void unit_vec(double lon, double lat, double& x, double& y,
+                                         double& z) {
+  double sb, cb, sl, cl;
+  sincos(lat * kDeg2Rad, &sb, &cb);
+  sincos(lon * kDeg2Rad, &sl, &cl);
+  x = cb * cl;
+  y = cb * sl;
+  z = sb;
+}
+
+__global__ void k_target_init(const double* __restrict__ lon, const double* __restrict__ lat,
+                              int64_t P, float4* __restrict__ pos, uint32_t* __restrict__ ord,
+                              uint32_t* __restrict__ nid, unsigned* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const double lo = lon[i], la = lat[i];
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid_coord(lo, la)) {
+    double x, y, z;
+    unit_vec(lo, la, x, y, z);
+    v = make_float4((float)x, (float)y, (float)z, 0.f);
+  } else {
+    set_error(err, ERR_BAD_TARGET);
+  }
+  pos[i] = v;
+  ord[i] = (uint32_t)i;
+  nid[i] = 0;
+}
+
+// First / one-past-last position of every node in the current order.
+__global__ void k_node_bounds(const uint32_t* __restrict__ nid, int64_t P,
+                              uint32_t* __restrict__ nstart, uint32_t* __restrict__ nend) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P) return;
+  const uint32_t n = nid[s];
+  if (s == 0 || nid[s - 1] != n) nstart[n] = (uint32_t)s;
+  if (s == P - 1 || nid[s + 1] != n) nend[n] = (uint32_t)(s + 1);
+}
+
+// Child of every position (left part = a multiple of kTile targets) and the
+// bounding box of every child (order-preserving integer min / max).
+__global__ void k_node_split(const uint32_t* __restrict__ nid, const uint32_t* __restrict__ ord,
+                             const float4* __restrict__ pos, int64_t P,
+                             const uint32_t* __restrict__ nstart,
+                             const uint32_t* __restrict__ nend, uint32_t* __restrict__ child,
+                             uint32_t* __restrict__ bmin, uint32_t* __restrict__ bmax) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P) return;
+  const uint32_t n = nid[s];
+  const uint32_t st = nstart[n], cnt = nend[n] - st;
+  uint32_t c = 2u * n;
+  if (cnt > (uint32_t)kTile) {
+    const uint32_t m = (cnt + kTile - 1) / kTile;
+    const uint32_t left = (uint32_t)kTile * (m / 2);
+    if ((uint32_t)s - st >= left) c += 1u;
+  }
+  child[s] = c;
+  const float4 v = pos[ord[s]];
+  atomicMin(&bmin[3 * c + 0], orderable(v.x));
+  atomicMin(&bmin[3 * c + 1], orderable(v.y));
+  atomicMin(&bmin[3 * c + 2], orderable(v.z));
+  atomicMax(&bmax[3 * c + 0], orderable(v.x));
+  atomicMax(&bmax[3 * c + 1], orderable(v.y));
+  atomicMax(&bmax[3 * c + 2], orderable(v.z));
+}
+
+__device__ __forceinline__ float from_orderable(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Sort key: (child node, coordinate along the child's widest axis).
+__global__ void k_node_keys(const uint32_t* __restrict__ child, const uint32_t* __restrict__ ord,
+                            const float4* __restrict__ pos, int64_t P,
+                            const uint32_t* __restrict__ bmin, const uint32_t* __restrict__ bmax,
+                            uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P) return;
+  const uint32_t c = child[s];
+  const float ex = from_orderable(bmax[3 * c + 0]) - from_orderable(bmin[3 * c + 0]);
+  const float ey = from_orderable(bmax[3 * c + 1]) - from_orderable(bmin[3 * c + 1]);
+  const float ez = from_orderable(bmax[3 * c + 2]) - from_orderable(bmin[3 * c + 2]);
+  const uint32_t o = ord[s];
+  const float4 v = pos[o];
+  const float coord = (ex >= ey && ex >= ez) ? v.x : ((ey >= ez) ? v.y : v.z);
+  key[s] = ((uint64_t)c << 32) | orderable(coord);
+  val[s] = o;
+}
+
+__global__ void k_node_unpack(const uint64_t* __restrict__ key, int64_t P,
+                              uint32_t* __restrict__ nid) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < P) nid[s] = (uint32_t)(key[s] >> 32);
+}
+
+// One CTA of kTile threads per tile.
+__global__ void __launch_bounds__(kTile) k_tile_build(
+    const double* __restrict__ lon, const double* __restrict__ lat, int64_t P,
+    const uint32_t* __restrict__ order, uint32_t* __restrict__ tgt_perm,
+    float4* __restrict__ tile_chi, float4* __restrict__ tile_clo, double4* __restrict__ tile_c64,
+    float4* __restrict__ tgt_a, float4* __restrict__ tgt_e, float4* __restrict__ tgt_n,
+    double2* __restrict__ tgt_ll) {
+  __shared__ double red[3][kTile];
+  const int64_t tile = blockIdx.x;
+  const int j = threadIdx.x;
+  const int64_t s = tile * kTile + j;
+  const bool valid = s < P;
+  double x = 0, y = 0, z = 0, lo = 0, la = 0;
+  uint32_t u = 0xffffffffu;
+  if (valid) {
+    u = order[s];
+    lo = lon[u];
+    la = lat[u];
+    unit_vec(lo, la, x, y, z);
+  }
+  red[0][j] = x;
+  red[1][j] = y;
+  red[2][j] = z;
+  __syncthreads();
+  for (int o = kTile / 2; o > 0; o >>= 1) {
+    if (j < o) {
+      red[0][j] += red[0][j + o];
+      red[1][j] += red[1][j + o];
+      red[2][j] += red[2][j + o];
+    }
+    __syncthreads();
+  }
+  double cx = red[0][0], cy = red[1][0], cz = red[2][0];
+  double nrm = sqrt(cx * cx + cy * cy + cz * cz);
+  __syncthreads();
+  if (!(nrm > 1e-9)) {  // degenerate spread: use the first member
+    const uint32_t u0 = order[tile * kTile];
+    unit_vec(lon[u0], lat[u0], cx, cy, cz);
+    nrm = 1.0;
+  }
+  cx /= nrm;
+  cy /= nrm;
+  cz /= nrm;
+  const double dx = x - cx, dy = y - cy, dz = z - cz;
+  double ang = 0.0;
+  if (valid) {
+    const double ch = sqrt(dx * dx + dy * dy + dz * dz);
+    ang = 2.0 * asin(fmin(1.0, 0.5 * ch));
+  }
+  red[0][j] = ang;
+  __syncthreads();
+  for (int o = kTile / 2; o > 0; o >>= 1) {
+    if (j < o) red[0][j] = fmax(red[0][j], red[0][j + o]);
+    __syncthreads();
+  }
+  const double radius = red[0][0] * (1.0 + 1e-9) + 1e-12;
+  tgt_perm[s] = valid ? u : 0xffffffffu;
+  if (valid) {
+    tgt_a[s] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+    double sl, cl, sb, cb;
+    sincos(lo * kDeg2Rad, &sl, &cl);
+    sincos(la * kDeg2Rad, &sb, &cb);
+    tgt_e[s] = make_float4((float)(-sl), (float)cl, 0.f, 0.f);
+    tgt_n[s] = make_float4((float)(-sb * cl), (float)(-sb * sl), (float)cb, 0.f);
+    tgt_ll[s] = make_double2(lo, la);
+  } else {
+    // an empty slot sits far outside every support radius
+    tgt_a[s] = make_float4(4.f, 4.f, 4.f, 0.f);
+    tgt_e[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tgt_n[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tgt_ll[s] = make_double2(0.0, 0.0);
+  }
+  if (j == 0) {
+    float hx, lx, hy, ly, hz, lz;
+    split_f64(cx, hx, lx);
+    split_f64(cy, hy, ly);
+    split_f64(cz, hz, lz);
+    tile_chi[tile] = make_float4(hx, hy, hz, (float)radius);
+    tile_clo[tile] = make_float4(lx, ly, lz, 0.f);
+    tile_c64[tile] = make_double4(cx, cy, cz, radius);
+  }
+}
+
+__global__ void k_set_axes(const float4* __restrict__ e, const float4* __restrict__ n,
+                           float4* __restrict__ f1, float4* __restrict__ f2, int64_t slots,
+                           float cpa, float spa) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= slots) return;
+  const float4 E = e[i], N = n[i];
+  // major axis at position angle PA from north through east
+  f1[i] = make_float4(N.x * cpa + E.x * spa, N.y * cpa + E.y * spa, N.z * cpa + E.z * spa, 0.f);
+  f2[i] = make_float4(E.x * cpa - N.x * spa, E.y * cpa - N.y * spa, E.z * cpa - N.z * spa, 0.f);
+}
+
+}  // namespace
+
+cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
+  cudaStream_t s = g->stream;
+  const int64_t P = g->P;
+  g->n_tiles = (P + kTile - 1) / kTile;
+  const int64_t slots = g->n_tiles * kTile;
+  cudaError_t e;
+  if ((e = dalloc(&g->tgt_perm, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tile_chi, g->n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tile_clo, g->n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tile_c64, g->n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_a, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_e, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_n, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_f1, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_f2, slots, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->tgt_ll, slots, s)) != cudaSuccess) return e;
+
+  // levels of the k-d tree: each level halves the number of tiles per node
+  int levels = 0;
+  while (((int64_t)1 << levels) < (int64_t)g->n_tiles) ++levels;
+  const int64_t max_nodes = (int64_t)1 << (levels + 1);
+  float4* pos = nullptr;
+  uint32_t *ord = nullptr, *nid = nullptr, *child = nullptr, *val = nullptr;
+  uint32_t *nstart = nullptr, *nend = nullptr, *bmin = nullptr, *bmax = nullptr;
+  uint64_t* key = nullptr;
+  SortWork w;
+  e = dalloc(&pos, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&ord, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&nid, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&child, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&val, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&key, (size_t)P, s);
+  if (e == cudaSuccess) e = dalloc(&nstart, (size_t)max_nodes, s);
+  if (e == cudaSuccess) e = dalloc(&nend, (size_t)max_nodes, s);
+  if (e == cudaSuccess) e = dalloc(&bmin, (size_t)(3 * max_nodes), s);
+  if (e == cudaSuccess) e = dalloc(&bmax, (size_t)(3 * max_nodes), s);
+  const unsigned nb = ceil_div(P, 256);
+  if (e == cudaSuccess) {
+    k_target_init<<<nb, 256, 0, s>>>(lon, lat, P, pos, ord, nid, g->d_err);
+    g->n_launches += 1;
+  }
+  for (int l = 0; l < levels && e == cudaSuccess; ++l) {
+    const int64_t nchild = (int64_t)1 << (l + 1);
+    e = cudaMemsetAsync(bmin, 0xff, sizeof(uint32_t) * (size_t)(3 * nchild), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bmax, 0x00, sizeof(uint32_t) * (size_t)(3 * nchild), s);
+    if (e != cudaSuccess) break;
+    k_node_bounds<<<nb, 256, 0, s>>>(nid, P, nstart, nend);
+    k_node_split<<<nb, 256, 0, s>>>(nid, ord, pos, P, nstart, nend, child, bmin, bmax);
+    k_node_keys<<<nb, 256, 0, s>>>(child, ord, pos, P, bmin, bmax, key, val);
+    g->n_launches += 3;
+    uint64_t* sk = nullptr;
+    uint32_t* sv = nullptr;
+    const int bits = 32 + l + 1;
+    e = radix_sort_u64(key, val, P, bits, w, s, &sk, &sv);
+    g->n_launches += 3 * ((bits + 7) / 8);
+    if (e != cudaSuccess) break;
+    k_node_unpack<<<nb, 256, 0, s>>>(sk, P, nid);
+    g->n_launches += 1;
+    if (sv != ord) e = cudaMemcpyAsync(ord, sv, sizeof(uint32_t) * (size_t)P,
+                                       cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) {
+    k_tile_build<<<(unsigned)g->n_tiles, kTile, 0, s>>>(
+        lon, lat, P, ord, g->tgt_perm, g->tile_chi, g->tile_clo, g->tile_c64, g->tgt_a, g->tgt_e,
+        g->tgt_n, g->tgt_ll);
+    g->n_launches += 1;
+    e = cudaGetLastError();
+  }
+  if (w.keys_alt) cudaFreeAsync(w.keys_alt, s);
+  dfree(w.vals_alt, s);
+  dfree(w.hist, s);
+  dfree(w.totals, s);
+  dfree(pos, s);
+  dfree(ord, s);
+  dfree(nid, s);
+  dfree(child, s);
+  dfree(val, s);
+  dfree(key, s);
+  dfree(nstart, s);
+  dfree(nend, s);
+  dfree(bmin, s);
+  dfree(bmax, s);
+  return e;
+}
+
+cudaError_t targets_set_axes(cg_grid* g, double pa_deg) {
+  const int64_t slots = g->n_tiles * kTile;
+  const double pa = pa_deg * kDeg2Rad;
+  k_set_axes<<<ceil_div(slots, 256), 256, 0, g->stream>>>(g->tgt_e, g->tgt_n, g->tgt_f1,
+                                                          g->tgt_f2, slots, (float)cos(pa),
+                                                          (float)sin(pa));
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,171 @@
+"""Python front end in the shape of the paper's Listing 1 (Sect. 3.5):
+
+    g = Gridder(lon_t, lat_t, n_channels)              # SlGrid: target sight lines
+    g.set_kernel("gauss1d", (sigma,), support, hpx_maxres)
+    g.grid(lon, lat, data)                             # accumulate (Eq. 1-2)
+    cube = g.get_datacube()                            # normalise (Eq. 3)
+
+Tensors are torch CUDA tensors (torch provides device memory and the stream);
+all arithmetic runs in the CUDA library behind the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi as C
+
+_KERNELS = {"gauss1d": C.CG_GAUSS1D, "gauss2d": C.CG_GAUSS2D}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_f64(x, device):
+    # build non-tensor inputs directly in float64 (torch would otherwise turn
+    # Python floats into float32 and round the coordinates)
+    t = x if isinstance(x, torch.Tensor) else torch.as_tensor(x, dtype=torch.float64)
+    return t.to(device=device, dtype=torch.float64).contiguous()
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Gridder:
+    """Convolution gridder onto a fixed list of target directions (degrees)."""
+
+    def __init__(self, lon_t, lat_t, n_channels: int = 1, device="cuda", stream=None):
+        self.device = torch.device(device)
+        self.lon_t = _dev_f64(lon_t, self.device)
+        self.lat_t = _dev_f64(lat_t, self.device)
+        self.n_targets = int(self.lon_t.numel())
+        self.n_channels = int(n_channels)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            C.cg_grid_create(ctypes.byref(h), _ptr(self.lon_t), _ptr(self.lat_t), self.n_targets,
+                             self.n_channels, _stream_handle(self.stream))
+        self._h = h
+
+    # -- kernel ---------------------------------------------------------
+    def set_kernel(self, kernel_type: str, kernel_params, support: float,
+                   hpx_maxres: float | None = None, nside: int = 0):
+        params = (ctypes.c_double * 3)(*([float(p) for p in kernel_params] + [0.0] * 3)[:3])
+        C.cg_set_kernel(self._h, _KERNELS[kernel_type], params, len(kernel_params),
+                        float(support), int(nside), float(hpx_maxres or 0.0))
+        return self
+
+    def set_path(self, path: int):
+        C.cg_set_path(self._h, int(path))
+        return self
+
+    # -- gridding -------------------------------------------------------
+    @staticmethod
+    def _data_dtype(data):
+        if data.dtype == torch.float32:
+            return C.CG_F32
+        if data.dtype == torch.bfloat16:
+            return C.CG_BF16
+        raise TypeError("data must be float32 or bfloat16")
+
+    def _prep(self, lon, lat, data, weights):
+        lon = _dev_f64(lon, self.device)
+        lat = _dev_f64(lat, self.device)
+        data = torch.as_tensor(data, device=self.device)
+        if data.dtype not in (torch.float32, torch.bfloat16):
+            data = data.to(torch.float32)
+        data = data.reshape(lon.numel(), self.n_channels).contiguous()
+        if weights is not None:
+            weights = torch.as_tensor(weights, device=self.device, dtype=torch.float32).contiguous()
+        return lon, lat, data, weights
+
+    def grid(self, lon, lat, data, weights=None):
+        lon, lat, data, weights = self._prep(lon, lat, data, weights)
+        C.cg_grid_add(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
+                      _ptr(weights), int(lon.numel()))
+        self._keep = (lon, lat, data, weights)   # alive until the stream has consumed them
+        return self
+
+    def get_datacube(self, channel_major: bool = False, out=None, out_weights=None):
+        shape = (self.n_channels, self.n_targets) if channel_major else \
+            (self.n_targets, self.n_channels)
+        if out is None:
+            out = torch.empty(shape, device=self.device, dtype=torch.float32)
+        C.cg_grid_finalize(self._h, _ptr(out), 1 if channel_major else 0, _ptr(out_weights))
+        return out
+
+    def get_weights(self):
+        w = torch.empty(self.n_targets, device=self.device, dtype=torch.float32)
+        tmp = torch.empty((self.n_targets, self.n_channels), device=self.device,
+                          dtype=torch.float32)
+        C.cg_grid_finalize(self._h, _ptr(tmp), 0, _ptr(w))
+        return w
+
+    def grid_oneshot(self, lon, lat, data, weights=None, out=None, out_weights=None,
+                     channel_major: bool = False):
+        lon, lat, data, weights = self._prep(lon, lat, data, weights)
+        shape = (self.n_channels, self.n_targets) if channel_major else \
+            (self.n_targets, self.n_channels)
+        if out is None:
+            out = torch.empty(shape, device=self.device, dtype=torch.float32)
+        C.cg_grid_oneshot(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
+                          _ptr(weights), int(lon.numel()), _ptr(out), 1 if channel_major else 0,
+                          _ptr(out_weights))
+        self._keep = (lon, lat, data, weights)
+        return out
+
+    def reset(self):
+        C.cg_grid_reset(self._h)
+
+    def sync(self):
+        C.cg_sync(self._h)
+
+    def info(self) -> dict:
+        inf = C.CgInfo()
+        C.cg_get_info(self._h, ctypes.byref(inf))
+        return {f: getattr(inf, f) for f, _ in C.CgInfo._fields_}
+
+    def export_index(self, n: int):
+        """(sorted RING indices, permutation, ring offsets) of the last add."""
+        pix = torch.empty(n, device=self.device, dtype=torch.int64)
+        perm = torch.empty(n, device=self.device, dtype=torch.int64)
+        ring = torch.empty(4 * self.info()["nside"] + 1, device=self.device, dtype=torch.int64)
+        C.cg_grid_export_index(self._h, _ptr(pix), _ptr(perm), _ptr(ring), int(n))
+        return pix, perm, ring
+
+    def set_timing(self, enable: bool = True):
+        C.cg_set_timing(self._h, 1 if enable else 0)
+
+    def read_timing(self) -> dict:
+        """Summed ms per stage since the previous read, and the gridder launch count."""
+        ms = (ctypes.c_double * C.CG_N_STAGES)()
+        n = ctypes.c_int64()
+        C.cg_read_timing(self._h, ms, ctypes.byref(n))
+        out = {name: ms[i] for i, name in enumerate(C.STAGE_NAMES)}
+        out["grid_launches"] = n.value
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            C.cg_grid_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ang2pix_ring(nside: int, lon, lat, stream=None):
+    """RING HEALPix index of each direction (int64 tensor, -1 if invalid)."""
+    lon = _dev_f64(lon, "cuda")
+    lat = _dev_f64(lat, "cuda")
+    pix = torch.empty(lon.numel(), device=lon.device, dtype=torch.int64)
+    C.cg_ang2pix_ring(int(nside), _ptr(lon), _ptr(lat), int(lon.numel()), _ptr(pix),
+                      _stream_handle(stream))
+    return pix

@@ -42,6 +42,12 @@ FFMA_LANES_PER_SM = 128
 N_SMS = 152
 
 
+def progress(msg):
+    """Progress marker on stderr (flushed), so a crash can be located."""
+    sys.stderr.write("[bench] %s\n" % msg)
+    sys.stderr.flush()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,46 +223,22 @@ def run_reference(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    import numpy as np
+def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks, peaks_src):
+    """Warm up, then time K one-shot steps of one accumulation form."""
     import torch
-    import workloads
-    from paper_1604_06667_gb300 import Gridder, _capi
-
-    world, rank, local = dist_init()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    peaks, peaks_src = load_peaks()
-    wl = workloads.cube(scale=args.scale)
-    form = "fp32" if args.form == "auto" else args.form
-    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
-    lon = torch.from_numpy(wl.lon_s).to(dev)
-    lat = torch.from_numpy(wl.lat_s).to(dev)
-    data32 = torch.from_numpy(wl.data).to(dev)
-    data = data32.to(torch.bfloat16) if form == "bf16" else data32
-    dbytes = 2 if form == "bf16" else 4
-    if form == "bf16":
-        del data32
-    g = Gridder(wl.lon_t, wl.lat_t, n_channels=C, device=dev)
-    g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
-    out = torch.empty((P, C), device=dev, dtype=torch.float32)
-    out_w = torch.empty(P, device=dev, dtype=torch.float32)
+    from paper_1604_06667_gb300 import _capi
+    dev = out.device
+    g.set_path(_capi.CG_PATH_TC if form == "bf16" else _capi.CG_PATH_FP32)
     stream = torch.cuda.current_stream(dev)
 
     def step():
         g.grid_oneshot(lon, lat, data, out=out, out_weights=out_w)
 
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
         step()
-    g.sync()
+        g.sync()
+        progress("  warm-up step %d ok" % i)
     info0 = g.info()
-    pairs = info0["n_pairs"]
-    gold = golden_pairs("cube_scale%g" % args.scale)
-
-    # ---- timed region (device-resident inputs) ----
     g.set_timing(True)
     g.read_timing()
     sampler = ClockSampler(local)
@@ -276,55 +258,122 @@ def main():
     stages = g.read_timing()
     g.set_timing(False)
     info1 = g.info()
-    launches = info1["n_launches"] - info0["n_launches"]
     ms_max = max_over_ranks(ms, world)
-    upd_per_step = float(pairs) * C
-    value = upd_per_step * world / (ms_max / 1e3)
-
-    # dominant kernel: the tile gridder
+    pairs = info1["n_pairs"]
+    C = wl.n_channels
+    upd = float(pairs) * C
+    dbytes = 2 if form == "bf16" else 4
     t_grid = stages["grid"] / max(1, stages["grid_launches"])
-    fma_flops = 2.0 * upd_per_step
     if form == "fp32":
         peak_tf = N_SMS * FFMA_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach_tf = fma_flops / (t_grid / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach_tf / peak_tf, "traffic": None,
+        ach = 2.0 * upd / (t_grid / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": None,
                 "kernel": "k_grid_f32 (tile gridder, FP32 CUDA cores)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
     else:
         hbm = peaks["hbm_gbs"]
-        gbytes = algorithmic_bytes(wl, dbytes) / 1e9
-        ach = gbytes / (t_grid / 1e3)
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "tile gridder (BF16 tensor cores)",
-                "peak_source": peaks_src}
+        kbytes = grid_kernel_bytes(wl, dbytes)
+        ach = kbytes / (t_grid / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None,
+                "kernel": "k_grid_tc (tile gridder, BF16 tcgen05 + TMEM)",
+                "bytes_per_launch": kbytes, "peak_source": peaks_src,
+                "tensor_useful_tflops": 2.0 * upd / (t_grid / 1e3) / 1e12,
+                "tensor_peak_tflops": peaks.get("bf16_tflops")}
     step_bytes = algorithmic_bytes(wl, dbytes)
-    hbm_frac = step_bytes / (ms_max / 1e3) / 1e9 / peaks["hbm_gbs"]
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if form == "bf16" else "f32",
-        "data": "synthetic (seeded basket-weave raster cube; no dataset)",
-        "config": {"workload": workload_desc(wl, form), "form": form,
-                   "l2": "inputs larger than L2 (%d MB of channel data), no flush"
-                         % (N * C * dbytes // 2 ** 20),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "pairs_per_step": pairs,
-        "pairs_oracle": gold,
+    return {
+        "form": form, "value": upd * world / (ms_max / 1e3), "ms_per_step": ms_max,
+        "pairs": pairs, "updates_per_step": upd,
         "hbm_roofline": {"bytes_per_step": step_bytes,
                          "achieved_gbs": step_bytes / (ms_max / 1e3) / 1e9,
-                         "peak_gbs": peaks["hbm_gbs"], "frac": hbm_frac,
+                         "peak_gbs": peaks["hbm_gbs"],
+                         "frac": step_bytes / (ms_max / 1e3) / 1e9 / peaks["hbm_gbs"],
                          "peak_source": peaks_src},
         "roofline": roof,
         "stages_ms_per_step": {k: v / args.steps for k, v in stages.items()
                                if k != "grid_launches"},
-        "gpu_launches": launches,
+        "gpu_launches": info1["n_launches"] - info0["n_launches"],
         "clocks": clocks,
     }
 
+
+def grid_kernel_bytes(wl, dbytes):
+    """Algorithmic bytes of one gridder launch: every sample's channel row and
+    its sorted 32-byte position record read once, the map and weight map
+    written once."""
+    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
+    return N * (C * dbytes + 32) + P * (C * 4 + 4)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peaks_src = load_peaks()
+    progress("generating workload")
+    wl = workloads.cube(scale=args.scale)
+    forms = ["bf16", "fp32"] if args.form == "auto" else [args.form]
+    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
+    lon = torch.from_numpy(wl.lon_s).to(dev)
+    lat = torch.from_numpy(wl.lat_s).to(dev)
+    data32 = torch.from_numpy(wl.data).to(dev)
+    data16 = data32.to(torch.bfloat16)
+    progress("create")
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=C, device=dev)
+    progress("set_kernel")
+    g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
+    out = torch.empty((P, C), device=dev, dtype=torch.float32)
+    out_w = torch.empty(P, device=dev, dtype=torch.float32)
+    results = {}
+    for form in forms:
+        progress("timing form %s" % form)
+        data = data16 if form == "bf16" else data32
+        results[form] = time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local,
+                                  peaks, peaks_src)
+    prim = results[forms[0]]
+    form = prim["form"]
+    gold = golden_pairs("cube_scale%g" % args.scale)
+    line = {
+        "metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": prim["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if form == "bf16" else "f32",
+        "data": "synthetic (seeded basket-weave raster cube; no dataset)",
+        "config": {"workload": workload_desc(wl, form), "form": form,
+                   "l2": "inputs larger than L2 (%d MB of channel data), no flush"
+                         % (N * C * (2 if form == "bf16" else 4) // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pairs_per_step": prim["pairs"],
+        "pairs_oracle": (gold or {}).get("pairs"),
+        "hbm_roofline": prim["hbm_roofline"],
+        "roofline": prim["roofline"],
+        "stages_ms_per_step": prim["stages_ms_per_step"],
+        "gpu_launches": prim["gpu_launches"],
+        "clocks": prim["clocks"],
+        "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "hbm_roofline", "roofline",
+                                        "stages_ms_per_step", "clocks")}
+                  for f, r in results.items()},
+    }
+    if len(results) == 2:
+        line["mixed_over_fp32"] = results["bf16"]["value"] / results["fp32"]["value"]
+
     # ---- end to end: pinned host inputs, copies inside the timed region ----
     if not args.no_e2e:
+        progress("e2e")
+        from paper_1604_06667_gb300 import _capi
+        g.set_path(_capi.CG_PATH_TC if form == "bf16" else _capi.CG_PATH_FP32)
+        data = data16 if form == "bf16" else data32
+        dbytes = 2 if form == "bf16" else 4
+        stream = torch.cuda.current_stream(dev)
         h_lon = torch.from_numpy(wl.lon_s).pin_memory()
         h_lat = torch.from_numpy(wl.lat_s).pin_memory()
         h_data = data.cpu().pin_memory()
@@ -342,27 +391,30 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-        hb = N * 16 + N * C * dbytes
-        line["e2e"] = {"value": upd_per_step * world / (ms_e2e / 1e3), "unit": UNIT,
-                       "h2d_bytes_per_step": hb, "d2h_bytes_per_step": P * C * 4,
-                       "ms_per_step": ms_e2e}
+        upd = prim["updates_per_step"]
+        line["e2e"] = {"value": upd * world / (ms_e2e / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": N * 16 + N * C * dbytes,
+                       "d2h_bytes_per_step": P * C * 4, "ms_per_step": ms_e2e}
 
     # ---- CPU baseline: the FP64 oracle as it stands, rank 0 only ----
     if rank == 0 and world == 1 and not args.no_cpu:
+        progress("cpu baseline")
         rate, dt, n, npairs = cpu_oracle_rate(wl, args.cpu_samples)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%d random samples of the workload (%d pairs, %d "
                                           "channels) onto all %d targets, %.1f s"
                                           % (n, npairs, C, P, dt)}
-    g.close()
     if rank == 0:
         print(json.dumps(line))
+        sys.stdout.flush()
+    g.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

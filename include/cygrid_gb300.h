@@ -69,9 +69,16 @@ typedef enum {
 } cg_kernel;
 
 typedef enum {
-  CG_PATH_AUTO = 0, /* choose by channel count and data type */
-  CG_PATH_FP32 = 1, /* channel accumulation on FP32 CUDA cores */
-  CG_PATH_TC = 2    /* BF16 x BF16 -> FP32 on the tcgen05 tensor cores */
+  CG_PATH_AUTO = 0,   /* CG_PATH_TC for BF16 data with C >= 16 and C % 8 == 0,
+                         else CG_PATH_FP32 */
+  CG_PATH_FP32 = 1,   /* channel accumulation on FP32 CUDA cores (any data) */
+  CG_PATH_TC = 2,     /* BF16 data on the tcgen05 tensor cores, FP32 accumulation;
+                         each weight as a hi + lo pair of BF16 numbers (~16
+                         significant bits), so the result matches the FP64
+                         definition on the same BF16 data to ~1e-5 */
+  CG_PATH_TC_FAST = 3 /* as CG_PATH_TC with single BF16 weights (8 significant
+                         bits): half the tensor work; map error up to 2^-8 of
+                         S_pc = sum |omega w D| / W */
 } cg_path;
 
 /* Create a gridder for n_targets target directions (paper Sect. 3.5: WcsGrid

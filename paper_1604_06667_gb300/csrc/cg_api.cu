@@ -51,6 +51,7 @@ cudaEvent_t tmark(cg_grid* g) {
     return nullptr;
   }
   cudaEventRecord(e, g->stream);
+  g->ev_used.push_back(e);  // owned once here; stage records only refer to it
   return e;
 }
 
@@ -58,11 +59,11 @@ void tstage(cg_grid* g, int stage, cudaEvent_t a, cudaEvent_t b) {
   if (a && b) g->timing_recs.push_back(cg_grid::TimingRec{stage, a, b});
 }
 
+// Consecutive stages share their boundary event, so events are returned to
+// the pool from the ownership list (each exactly once), not from the records.
 void release_events(cg_grid* g) {
-  for (auto& r : g->timing_recs) {
-    g->ev_pool.push_back(r.a);
-    g->ev_pool.push_back(r.b);
-  }
+  for (cudaEvent_t e : g->ev_used) g->ev_pool.push_back(e);
+  g->ev_used.clear();
   g->timing_recs.clear();
 }
 
@@ -91,18 +92,13 @@ cg_status check_device(cg_grid* g, const char* where) {
 void free_all(cg_grid* g) {
   cudaStream_t s = g->stream;
   dfree(g->tgt_perm, s);
-  dfree(g->tile_chi, s);
-  dfree(g->tile_clo, s);
-  dfree(g->tile_c64, s);
-  dfree(g->tgt_a, s);
+  tiling_free(g->t64, s);
+  tiling_free(g->t128, s);
   dfree(g->tgt_e, s);
   dfree(g->tgt_n, s);
   dfree(g->tgt_f1, s);
   dfree(g->tgt_f2, s);
   dfree(g->tgt_ll, s);
-  dfree(g->range_off, s);
-  dfree(g->ranges, s);
-  dfree(g->range_s, s);
   dfree(g->key, s);
   dfree(g->val, s);
   if (g->sw.keys_alt) cudaFreeAsync(g->sw.keys_alt, s);
@@ -125,7 +121,7 @@ void free_all(cg_grid* g) {
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 cg_status zero_acc(cg_grid* g) {
-  const int64_t slots = g->n_tiles * kTile;
+  const int64_t slots = g->n_slots;
   CG_CUDA(cudaMemsetAsync(g->acc_num, 0, sizeof(float) * (size_t)slots * g->C, g->stream),
           "reset");
   CG_CUDA(cudaMemsetAsync(g->acc_w, 0, sizeof(float2) * (size_t)slots, g->stream), "reset");
@@ -135,8 +131,19 @@ cg_status zero_acc(cg_grid* g) {
   return CG_OK;
 }
 
+// Channel-accumulation form for this add.
+bool use_tc(const cg_grid* g, int dtype, const void* data) {
+  if (g->path == CG_PATH_FP32) return false;
+  if (g->path == CG_PATH_TC || g->path == CG_PATH_TC_FAST) return true;
+  return tc_supported(g, dtype, data) && g->C >= 16;
+}
+
+// out != nullptr: one-shot call whose normalised [P][C] result the
+// tensor-core epilogue writes directly (the accumulators are left empty).
 cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* data,
-                 int32_t dtype, const float* weights, int64_t n, const char* where) {
+                 int32_t dtype, const float* weights, int64_t n, const char* where,
+                 float* out = nullptr, float* out_w = nullptr, bool* fused = nullptr) {
+  if (fused) *fused = false;
   if (!g) return fail(CG_EINVAL, "%s: null handle", where);
   if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
   if (dtype != CG_F32 && dtype != CG_BF16)
@@ -144,23 +151,38 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
   if (n < 0 || n > 0x7fffffffLL) return fail(CG_EINVAL, "%s: n_samples out of range", where);
   if (n == 0) return CG_OK;
   if (!lon || !lat || !data) return fail(CG_EINVAL, "%s: null coordinate or data pointer", where);
+  const bool tc = use_tc(g, dtype, data);
+  if (tc && !tc_supported(g, dtype, data))
+    return fail(CG_EINVAL,
+                "%s: the tensor-core form needs BF16 data, n_channels %% 8 == 0 and a "
+                "16-byte aligned data pointer",
+                where);
   CG_CUDA(cudaSetDevice(g->device), where);
+  Tiling& t = tc ? g->t128 : g->t64;
   cudaEvent_t t0 = tmark(g);
   CG_CUDA(samples_keys(g, lon, lat, n), where);
   cudaEvent_t t1 = tmark(g);
   CG_CUDA(samples_sort(g, n), where);
   cudaEvent_t t2 = tmark(g);
-  CG_CUDA(samples_prepare(g, lon, lat, weights, n), where);
+  CG_CUDA(samples_prepare(g, lon, lat, weights, n, t), where);
   cudaEvent_t t3 = tmark(g);
-  CG_CUDA(grid_tiles_f32(g, data, dtype, lon, lat), where);
+  if (tc) {
+    const bool fuse = out != nullptr && g->acc_empty;
+    const int mode = fuse ? 2 : (g->acc_empty ? 0 : 1);
+    CG_CUDA(grid_tiles_tc(g, data, lon, lat, mode, out, out_w, g->path != CG_PATH_TC_FAST),
+            where);
+    if (fused) *fused = fuse;
+  } else {
+    CG_CUDA(grid_tiles_f32(g, data, dtype, lon, lat), where);
+  }
   cudaEvent_t t4 = tmark(g);
   tstage(g, 0, t0, t1);
   tstage(g, 1, t1, t2);
   tstage(g, 2, t2, t3);
   tstage(g, 3, t3, t4);
-  g->last_path = CG_PATH_FP32;
-  g->acc_empty = false;
+  g->last_path = tc ? (g->path == CG_PATH_TC_FAST ? CG_PATH_TC_FAST : CG_PATH_TC) : CG_PATH_FP32;
   g->total_n += n;
+  if (!(fused && *fused)) g->acc_empty = false;
   return CG_OK;
 }
 
@@ -190,7 +212,7 @@ cg_status cg_grid_create(cg_grid** out, const double* lon_deg, const double* lat
   if (e == cudaSuccess) e = dalloc(&g->d_pairs, 1, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), g->stream);
   if (e == cudaSuccess) e = targets_build(g, lon_deg, lat_deg);
-  const int64_t slots = g->n_tiles * kTile;
+  const int64_t slots = g->n_slots;
   if (e == cudaSuccess) e = dalloc(&g->acc_num, (size_t)slots * g->C, g->stream);
   if (e == cudaSuccess) e = dalloc(&g->acc_w, (size_t)slots, g->stream);
   if (e != cudaSuccess) {
@@ -268,7 +290,8 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
   kd.big_support = chord > 0.1 ? 1 : 0;
   g->kdev = kd;
   if (kernel_type == CG_GAUSS2D) CG_CUDA(targets_set_axes(g, pa), "cg_set_kernel");
-  CG_CUDA(tiles_query(g), "cg_set_kernel");
+  CG_CUDA(tiles_query(g, g->t64), "cg_set_kernel");
+  CG_CUDA(tiles_query(g, g->t128), "cg_set_kernel");
   cg_status st = zero_acc(g);
   if (st != CG_OK) return st;
   g->kernel_set = true;
@@ -305,8 +328,11 @@ cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_d
   CG_CUDA(cudaSetDevice(g->device), "cg_grid_oneshot");
   cg_status st = zero_acc(g);
   if (st != CG_OK) return st;
-  st = do_add(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, "cg_grid_oneshot");
+  bool fused = false;
+  st = do_add(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, "cg_grid_oneshot",
+              layout_channel_major ? nullptr : out, out_weights, &fused);
   if (st != CG_OK) return st;
+  if (fused) return CG_OK;  // the tensor-core epilogue already wrote Eq. 3
   cudaEvent_t t0 = tmark(g);
   CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_oneshot");
   tstage(g, 4, t0, tmark(g));
@@ -343,7 +369,8 @@ cg_status cg_set_stream(cg_grid* g, void* stream) {
 cg_status cg_set_path(cg_grid* g, int32_t path) {
   g_last_error.clear();
   if (!g) return fail(CG_EINVAL, "cg_set_path: null handle");
-  if (path < CG_PATH_AUTO || path > CG_PATH_TC) return fail(CG_EINVAL, "cg_set_path: bad path");
+  if (path < CG_PATH_AUTO || path > CG_PATH_TC_FAST)
+    return fail(CG_EINVAL, "cg_set_path: bad path");
   g->path = path;
   return CG_OK;
 }
@@ -361,10 +388,11 @@ cg_status cg_get_info(cg_grid* g, cg_info* info) {
   info->n_targets = g->P;
   info->n_channels = g->C;
   info->nside = g->nside;
-  info->n_tiles = g->n_tiles;
-  info->tile_size = kTile;
+  const bool tc = g->last_path == CG_PATH_TC || g->last_path == CG_PATH_TC_FAST;
+  info->n_tiles = tc ? g->t128.n_tiles : g->t64.n_tiles;
+  info->tile_size = tc ? kTile2 : kTile;
   info->path = g->last_path;
-  info->n_ranges = g->n_ranges;
+  info->n_ranges = tc ? g->t128.n_ranges : g->t64.n_ranges;
   info->n_samples_total = g->total_n;
   info->n_launches = g->n_launches;
   unsigned long long pairs = 0;

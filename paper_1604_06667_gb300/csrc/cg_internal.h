@@ -14,8 +14,11 @@
 
 namespace cg {
 
-// Tile size: targets grouped per CTA.
+// Tile sizes: targets grouped per CTA (FP32 form: 64; tensor-core form: 128,
+// the M dimension of one tcgen05 MMA).  The 128-tiles are unions of two
+// sibling 64-tiles, so both tilings share one slot layout.
 constexpr int kTile = 64;
+constexpr int kTile2 = 128;
 // Candidate samples staged per chunk.
 constexpr int kChunk = 32;
 
@@ -33,6 +36,20 @@ struct KernelDev {        // kernel constants used by the gridder
   float c2_cut;           // chord^2 of the support radius
   double r_rad;           // support radius (FP64 guard-band decision)
   int big_support;        // 1 if the chord series for d^2 is not accurate enough
+};
+
+struct Tiling {           // geometry of one tiling of the targets
+  int T = 0;
+  int64_t n_tiles = 0;
+  float4* chi = nullptr;          // [n_tiles] centre hi (xyz), w = radius (rad)
+  float4* clo = nullptr;          // [n_tiles] centre lo (xyz)
+  double4* c64 = nullptr;         // [n_tiles] FP64 centre, w = radius
+  float4* a = nullptr;            // [n_tiles*T] u_t - centre (FP32)
+  int64_t n_ranges = 0;
+  int64_t* range_off = nullptr;   // [n_tiles + 1]
+  Range* ranges = nullptr;        // [n_ranges]
+  int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi) of the last add
+  int32_t* tile_cand = nullptr;   // [n_tiles] candidates per tile of the last add
 };
 
 struct SortWork {         // radix-sort scratch
@@ -53,13 +70,10 @@ struct cg_grid {
   int32_t path = CG_PATH_AUTO;
   int32_t last_path = CG_PATH_FP32;
 
-  // targets, in tile order (slot = tile * kTile + lane; empty slots marked)
-  int64_t n_tiles = 0;
-  uint32_t* tgt_perm = nullptr;   // [n_tiles*kTile] user index or 0xffffffff
-  float4* tile_chi = nullptr;     // [n_tiles] centre hi (xyz), w = radius (rad)
-  float4* tile_clo = nullptr;     // [n_tiles] centre lo (xyz)
-  double4* tile_c64 = nullptr;    // [n_tiles] FP64 centre (xyz), w = radius
-  float4* tgt_a = nullptr;        // [slots] u_t - centre (FP32)
+  // targets, in tile order (slot = tile * T + lane; empty slots marked)
+  cg::Tiling t64, t128;
+  int64_t n_slots = 0;            // t128.n_tiles * kTile2 (>= t64.n_tiles * kTile)
+  uint32_t* tgt_perm = nullptr;   // [n_slots] user index or 0xffffffff
   float4* tgt_e = nullptr;        // [slots] local east unit vector
   float4* tgt_n = nullptr;        // [slots] local north unit vector
   float4* tgt_f1 = nullptr;       // [slots] major-axis direction (set_kernel)
@@ -73,9 +87,6 @@ struct cg_grid {
   double support_deg = 0;
   int32_t nside = 0;
   cg::KernelDev kdev{};
-  int64_t n_ranges = 0;
-  int64_t* range_off = nullptr;   // [n_tiles + 1]
-  cg::Range* ranges = nullptr;    // [n_ranges]
 
   // per-add sample workspace
   size_t cap_n = 0;
@@ -87,7 +98,6 @@ struct cg_grid {
   float4* s_hi = nullptr;         // [cap_n] sorted samples: unit vector hi, w = omega
   float4* s_lo = nullptr;         // [cap_n] unit vector lo
   int32_t* ring_off = nullptr;    // [4*nside + 1]
-  int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi)
   int64_t last_n = 0;
   int64_t total_n = 0;
 
@@ -106,8 +116,9 @@ struct cg_grid {
     cudaEvent_t a, b;
   };
   bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<TimingRec> timing_recs;
+  std::vector<cudaEvent_t> ev_pool;   // idle events
+  std::vector<cudaEvent_t> ev_used;   // events handed out since the last read
+  std::vector<TimingRec> timing_recs; // stages refer to events in ev_used
 };
 
 namespace cg {
@@ -130,14 +141,21 @@ cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int6
 cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, int64_t n);
 cudaError_t samples_sort(cg_grid* g, int64_t n);
 cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
-                            const float* weights, int64_t n);
-cudaError_t tiles_query(cg_grid* g);
+                            const float* weights, int64_t n, Tiling& t);
+cudaError_t tiles_query(cg_grid* g, Tiling& t);
+void tiling_free(Tiling& t, cudaStream_t s);
 cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t* ring_off,
                          int64_t n);
 
 // k_grid.cu -- the tile gridder (FP32 CUDA-core form).
 cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
                            const double* lat);
+// k_grid_tc.cu -- the tile gridder, BF16 tcgen05 form (TMEM accumulators).
+// mode 0: store into the accumulators, 1: add into them, 2: one-shot
+// normalised output in the caller's [P][C] layout (out, out_w).
+bool tc_supported(const cg_grid* g, int dtype, const void* data);
+cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
+                          int mode, float* out, float* out_w, int split);
 // k_finalize.cu -- normalisation and output layout.
 cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w);
 

@@ -28,7 +28,7 @@ __global__ void k_finalize(const float* __restrict__ num, const float2* __restri
 }  // namespace
 
 cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w) {
-  const int64_t slots = g->n_tiles * kTile;
+  const int64_t slots = g->n_slots;
   const int64_t total = slots * g->C;
   k_finalize<<<ceil_div(total, 256), 256, 0, g->stream>>>(g->acc_num, g->acc_w, g->tgt_perm,
                                                          slots, g->C, g->P, channel_major, out,

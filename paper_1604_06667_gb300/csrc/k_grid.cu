@@ -189,7 +189,8 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
           sh_lo[tid] = a.s_lo[s];
           sh_idx[tid] = a.perm[s];
         } else {
-          sh_hi[tid] = make_float4(4.f, 4.f, 4.f, 0.f);
+          // padding candidate (never equal to an empty target slot's sentinel)
+          sh_hi[tid] = make_float4(-4.f, -4.f, -4.f, 0.f);
           sh_lo[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
           sh_idx[tid] = 0xffffffffu;
         }
@@ -358,15 +359,15 @@ cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s
 cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
                            const double* lat) {
   GridArgs a;
-  a.tile_chi = g->tile_chi;
-  a.tile_clo = g->tile_clo;
-  a.tgt_a = g->tgt_a;
+  a.tile_chi = g->t64.chi;
+  a.tile_clo = g->t64.clo;
+  a.tgt_a = g->t64.a;
   a.tgt_f1 = g->tgt_f1;
   a.tgt_f2 = g->tgt_f2;
   a.tgt_ll = g->tgt_ll;
   a.tgt_perm = g->tgt_perm;
-  a.range_off = g->range_off;
-  a.range_s = g->range_s;
+  a.range_off = g->t64.range_off;
+  a.range_s = g->t64.range_s;
   a.s_hi = g->s_hi;
   a.s_lo = g->s_lo;
   a.perm = g->sorted_val;
@@ -383,7 +384,7 @@ cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double
   a.pairs = g->d_pairs;
   g->n_launches += 1;
   const int C = g->C;
-  const int64_t nt = g->n_tiles;
+  const int64_t nt = g->t64.n_tiles;
   cudaStream_t s = g->stream;
   if (C <= 4) return launch<1, 4, 1>(a, nt, dtype, s);
   if (C <= 8) return launch<1, 8, 1>(a, nt, dtype, s);

@@ -1,0 +1,651 @@
+// k_grid_tc.cu -- tile gridder, BF16 tensor-core form (paper Eq. 1-3).
+//
+// For a tile of 128 targets and a chunk of 32 candidate samples the kernel
+// evaluates the weight matrix A[p][k] = omega_k w(p, k) (BF16) on the CUDA
+// cores and accumulates D[p][c] += sum_k A[p][k] B[k][c] with B the samples'
+// BF16 channel rows, on the tcgen05 tensor cores with FP32 accumulators in
+// tensor memory (TMEM):
+//
+//   M = 128 targets (TMEM lanes), N = channels of one slab (<= 256, TMEM
+//   columns), K = candidates, two K = 16 MMAs per chunk.
+//
+// Operands: A lives in TMEM (written with tcgen05.st by the thread that owns
+// the target row, so the weights never touch shared memory).  In the default
+// (split) form every weight is stored as w_hi + w_lo, two BF16 numbers
+// (~16 significant bits), and each K step issues one MMA per half against
+// the same B; the fast form keeps only w_hi (8 significant bits).  B is staged in
+// shared memory in the MN-major, unswizzled canonical layout (8 channels x
+// 8 candidates per 128-byte core matrix; LBO = 128 B between candidate
+// blocks, SBO = 512 B between channel blocks).
+//
+// Warp roles (persistent CTA, static round-robin over (tile, slab) items):
+//   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 and
+//              candidates 16 (w / 4) .. + 15 of every chunk; weight-map sums
+//              from the same BF16-rounded weights the MMA consumes; epilogue;
+//   warp 8     producer: walks the tile's sample ranges, writes tile-relative
+//              candidate vectors and stages data rows with cp.async;
+//   warp 9     MMA issue (one lane) and tcgen05.commit.
+// Every mbarrier wait is bounded; on time-out the kernel records
+// ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
+#include <cuda_bf16.h>
+
+#include "cg_common.cuh"
+#include "cg_internal.h"
+
+namespace cg {
+namespace {
+
+constexpr int kT = kTile2;          // targets per tile = MMA M
+constexpr int kK = 32;              // candidates per chunk
+constexpr int kWW = 8;              // weight warps
+constexpr int kThreads = (kWW + 2) * 32;
+constexpr int kProdWarp = kWW;
+constexpr int kMmaWarp = kWW + 1;
+constexpr int kMaxStages = 8;
+// a wait gives up after ~1 s of SM clock (or at once after another role gave up)
+constexpr long long kWaitCycles = 2000000000LL;
+
+struct TcArgs {
+  const float4* chi;
+  const float4* clo;
+  const float4* ta;
+  const int64_t* range_off;
+  const int2* range_s;
+  const int32_t* tile_cand;
+  int64_t n_tiles;
+  const float4* f1;
+  const float4* f2;
+  const double2* tll;
+  const uint32_t* perm_t;
+  const float4* s_hi;
+  const float4* s_lo;
+  const uint32_t* sperm;
+  const double* lon;
+  const double* lat;
+  const __nv_bfloat16* data;
+  int C;
+  int cp;        // padded channels per slab (multiple of 32, <= 256)
+  int n_slabs;
+  int ns;        // pipeline stages
+  int split;     // 1: weights as hi + lo BF16 pairs (two MMAs per K step)
+  uint32_t tmem_cols;
+  KernelDev kd;
+  int mode;      // 0 store, 1 add, 2 one-shot normalised output
+  float* acc_num;
+  float2* acc_w;
+  float* out;
+  float* out_w;
+  int64_t P;
+  int64_t n_slots;
+  unsigned long long* pairs;
+  unsigned* err;
+};
+
+struct Smem {
+  uint8_t* B;          // ns stages of cp * 64 bytes
+  float4* cand;        // ns x kK
+  uint32_t* cidx;      // ns x kK
+  float2* wpart;       // 2 buffers x kWW/4 x kT partial weight sums
+  uint64_t* full;      // ns
+  uint64_t* afull;     // ns
+  uint64_t* empty;     // ns
+  uint64_t* dfull;
+  uint64_t* dempty;
+  uint64_t* fin;
+  uint64_t* wbar;
+  uint32_t* tmem_base;
+  int* abort_flag;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(su32(b))
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity: false on time-out or
+// when another role has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity,
+                                          volatile int* abort_flag) {
+  const uint32_t a = su32(b);
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __noinline__ double haversine_f64(double l1, double b1, double l2, double b2) {
+  const double p1 = b1 * kDeg2Rad, p2 = b2 * kDeg2Rad;
+  const double dl = (l2 - l1) * kDeg2Rad;
+  const double sdp = sin(0.5 * (p2 - p1));
+  const double sdl = sin(0.5 * dl);
+  double h = sdp * sdp + cos(p1) * cos(p2) * sdl * sdl;
+  h = fmin(h, 1.0);
+  return 2.0 * asin(sqrt(h));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const int ns = a.ns;
+  const int cp = a.cp;
+  Smem S;
+  {
+    uint8_t* p = smem_raw;
+    S.B = p;
+    p += (size_t)ns * cp * 64;
+    S.cand = reinterpret_cast<float4*>(p);
+    p += (size_t)ns * kK * sizeof(float4);
+    S.cidx = reinterpret_cast<uint32_t*>(p);
+    p += (size_t)ns * kK * sizeof(uint32_t);
+    S.wpart = reinterpret_cast<float2*>(p);
+    p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);
+    S.full = reinterpret_cast<uint64_t*>(p);
+    S.afull = S.full + kMaxStages;
+    S.empty = S.afull + kMaxStages;
+    S.dfull = S.empty + kMaxStages;
+    S.dempty = S.dfull + 1;
+    S.fin = S.dempty + 1;
+    S.wbar = S.fin + 1;
+    S.tmem_base = reinterpret_cast<uint32_t*>(S.wbar + 1);
+    S.abort_flag = reinterpret_cast<int*>(S.tmem_base + 1);
+  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(S.tmem_base)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&S.full[s], 64);        // 32 staging stores + 32 cp.async completions
+      mbar_init(&S.afull[s], kWW * 32);  // every weight thread
+      mbar_init(&S.empty[s], 1);        // MMA commit
+    }
+    mbar_init(S.dfull, 1);
+    mbar_init(S.dempty, kWW * 32);
+    mbar_init(S.fin, 1);
+    mbar_init(S.wbar, kWW * 32);
+    *S.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *S.tmem_base;
+  const uint32_t tmem_d = tmem;              // columns [0, cp)
+  const uint32_t acols = a.split ? 32u : 16u;   // TMEM columns of A per stage
+  const uint32_t tmem_a = tmem + (uint32_t)cp;  // columns [cp, cp + acols ns)
+  const int64_t n_items = a.n_tiles * a.n_slabs;
+  volatile int* abort_flag = S.abort_flag;
+
+  if (warp == kProdWarp) {
+    // ------------------------------------------------------------ producer
+    uint32_t q = 0;
+    const uint32_t piece_per_row = (uint32_t)cp / 8;
+    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+      const int64_t tile = item / a.n_slabs;
+      const int c_base = (int)(item % a.n_slabs) * cp;
+      const float4 chi = a.chi[tile], clo = a.clo[tile];
+      const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
+      const int total = a.tile_cand[tile];
+      const int nch = (total + kK - 1) / kK;
+      // window of 32 ranges held in lanes
+      int64_t wnext = r0;
+      int wr = 32, off = 0;
+      int2 wrange = make_int2(0, 0);
+      for (int ch = 0; ch < nch; ++ch, ++q) {
+        const int st = (int)(q % (uint32_t)ns);
+        if (q >= (uint32_t)ns) {
+          if (!mbar_wait(&S.empty[st], ((q / ns) - 1) & 1, abort_flag)) {
+            set_error(a.err, ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+          }
+        }
+        // gather the sorted positions of this chunk's candidates
+        // (every pass either fills candidates or moves to the next range)
+        int mypos = -1;
+        int filled = 0;
+        while (filled < kK) {
+          if (wr == 32) {
+            const int64_t r = wnext + lane;
+            wrange = (r < r1) ? a.range_s[r] : make_int2(0, 0);
+            wnext += 32;
+            wr = 0;
+            off = 0;
+            if (wnext - 32 >= r1) break;
+          }
+          const int rs = __shfl_sync(0xffffffffu, wrange.x, wr);
+          const int re = __shfl_sync(0xffffffffu, wrange.y, wr);
+          const int avail = re - rs - off;
+          const int take = min(kK - filled, avail);
+          if (take > 0 && lane >= filled && lane < filled + take) mypos = rs + off + (lane - filled);
+          filled += max(take, 0);
+          off += max(take, 0);
+          if (off >= re - rs) {
+            ++wr;
+            off = 0;
+          }
+        }
+        // padding candidate: far from every target and from the empty-slot
+        // sentinel (4, 4, 4) of the tile-relative target vectors
+        float4 cb = make_float4(-4.f, -4.f, -4.f, 0.f);
+        uint32_t idx = 0xffffffffu;
+        if (mypos >= 0) {
+          const float4 h = a.s_hi[mypos];
+          const float4 l = a.s_lo[mypos];
+          idx = a.sperm[mypos];
+          cb = make_float4(df_diff(h.x, l.x, chi.x, clo.x), df_diff(h.y, l.y, chi.y, clo.y),
+                           df_diff(h.z, l.z, chi.z, clo.z), h.w);
+        }
+        S.cand[st * kK + lane] = cb;
+        S.cidx[st * kK + lane] = idx;
+        __syncwarp();
+        // data rows -> B stage (MN-major core matrices)
+        const uint32_t bbase = su32(S.B + (size_t)st * cp * 64);
+        const uint32_t npieces = (uint32_t)kK * piece_per_row;
+        for (uint32_t pc = lane; pc < npieces; pc += 32) {
+          const uint32_t k = pc / piece_per_row, nb = pc % piece_per_row;
+          const uint32_t rid = S.cidx[st * kK + k];
+          const int c0 = c_base + (int)nb * 8;
+          const bool ok = (rid != 0xffffffffu) && (c0 < a.C);
+          const __nv_bfloat16* src = ok ? a.data + (size_t)rid * a.C + c0 : a.data;
+          const uint32_t dst = bbase + nb * 512u + (k >> 3) * 128u + (k & 7u) * 16u;
+          cp_async16(dst, src, ok ? 16u : 0u);
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         su32(&S.full[st]))
+                     : "memory");
+        mbar_arrive(&S.full[st]);
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      uint32_t q = 0, tq = 0;
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
+                             ((uint32_t)(cp >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+      for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+        const int64_t tile = item / a.n_slabs;
+        const int nch = (a.tile_cand[tile] + kK - 1) / kK;
+        if (tq > 0 && !mbar_wait(S.dempty, (tq - 1) & 1, abort_flag)) {
+          set_error(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        bool ok = true;
+        for (int ch = 0; ch < nch; ++ch, ++q) {
+          const int st = (int)(q % (uint32_t)ns);
+          const uint32_t ph = (q / ns) & 1;
+          if (!mbar_wait(&S.full[st], ph, abort_flag) ||
+              !mbar_wait(&S.afull[st], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const uint32_t bstage = su32(S.B + (size_t)st * cp * 64);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t bd = smem_desc(bstage + kk * 256u, 128u, 512u);
+            const int halves = a.split ? 2 : 1;
+            for (int h = 0; h < halves; ++h) {
+              // A of candidates 16 kk .. 16 kk + 15: hi at +0, lo at +8 columns
+              const uint32_t at = tmem_a + st * acols + (uint32_t)(kk * (a.split ? 16 : 8) + h * 8);
+              const uint32_t acc = (ch > 0 || kk > 0 || h > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+                  "r"(at), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
+            }
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  su32(&S.empty[st]))
+              : "memory");
+        }
+        if (!ok) {
+          set_error(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(S.dfull))
+            : "memory");
+      }
+      // completion of everything this thread issued, before TMEM is freed
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(S.fin))
+          : "memory");
+    }
+  } else {
+    // ------------------------------------------------------------ weights
+    const int row = (warp & 3) * 32 + lane;   // TMEM lane = target row
+    const int grp = warp >> 2;                // candidate half
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int half_cols = cp / 2;             // epilogue columns of this group
+    uint32_t q = 0, tq = 0;
+    unsigned npair = 0;
+    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+      const int64_t tile = item / a.n_slabs;
+      const int slab = (int)(item % a.n_slabs);
+      const int c_base = slab * cp;
+      const int64_t slot = tile * kT + row;
+      if (slot >= a.n_slots) set_error(a.err, ERR_INTERNAL);
+      const float4 at = a.ta[slot];
+      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
+      if (a.kd.type == CG_GAUSS2D) {
+        f1 = a.f1[slot];
+        f2 = a.f2[slot];
+      }
+      const uint32_t user = a.perm_t[slot];
+      const int nch = (a.tile_cand[tile] + kK - 1) / kK;
+      float ws = 0.f, wc = 0.f;
+      bool ok = true;
+      for (int ch = 0; ch < nch; ++ch, ++q) {
+        const int st = (int)(q % (uint32_t)ns);
+        if (!mbar_wait(&S.full[st], (q / ns) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        uint32_t packed[8], packed_lo[8];
+        float part = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float wpair[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = grp * 16 + 2 * j + h;
+            const float4 cb = S.cand[st * kK + k];
+            const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
+            const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float w = 0.f;
+            if (c2 <= a.kd.c2_out) {
+              float d2;
+              if (!a.kd.big_support) {
+                d2 = c2 * fmaf(c2, fmaf(c2, 1.f / 90.f, 1.f / 12.f), 1.f);
+              } else {
+                const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+                d2 = d * d;
+              }
+              float ex;
+              if (a.kd.type == CG_GAUSS1D) {
+                ex = a.kd.k1 * d2;
+              } else {
+                const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+                const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+                const float s2 = fmaf(ap, ap, bp * bp);
+                const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+                ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
+              }
+              w = ex2_approx(ex) * cb.w;
+              bool inside = true;
+              if (c2 >= a.kd.c2_in) {
+                const uint32_t idx = S.cidx[st * kK + k];
+                const double2 tl = a.tll[slot];
+                const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+                inside = d <= a.kd.r_rad;
+              }
+              if (!inside) w = 0.f;
+              else if (slab == 0) ++npair;
+            }
+            wpair[h] = w;
+          }
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(wpair[0], wpair[1]);
+          const float2 back = __bfloat1622float2(b2);
+          packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
+          if (a.split) {
+            // w_lo = w - w_hi; the weight map sums the weights the MMAs see
+            const __nv_bfloat162 l2 =
+                __floats2bfloat162_rn(wpair[0] - back.x, wpair[1] - back.y);
+            const float2 lback = __bfloat1622float2(l2);
+            packed_lo[j] = *reinterpret_cast<const uint32_t*>(&l2);
+            part += (back.x + lback.x) + (back.y + lback.y);
+          } else {
+            packed_lo[j] = 0u;
+            part += back.x + back.y;
+          }
+        }
+        // Kahan accumulation of the chunk partial into the weight map
+        {
+          const float y = part - wc;
+          const float t = ws + y;
+          wc = (t - ws) - y;
+          ws = t;
+        }
+        if (a.split) {
+          const uint32_t ta_addr = tmem_a + lane_off + st * acols + (uint32_t)(grp * 16);
+          asm volatile(
+              "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+              "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta_addr),
+              "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3]), "r"(packed[4]),
+              "r"(packed[5]), "r"(packed[6]), "r"(packed[7]), "r"(packed_lo[0]),
+              "r"(packed_lo[1]), "r"(packed_lo[2]), "r"(packed_lo[3]), "r"(packed_lo[4]),
+              "r"(packed_lo[5]), "r"(packed_lo[6]), "r"(packed_lo[7])
+              : "memory");
+        } else {
+          const uint32_t ta_addr = tmem_a + lane_off + st * acols + (uint32_t)(grp * 8);
+          asm volatile(
+              "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                  ta_addr),
+              "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3]), "r"(packed[4]),
+              "r"(packed[5]), "r"(packed[6]), "r"(packed[7])
+              : "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        mbar_arrive(&S.afull[st]);
+      }
+      // ---- epilogue: combine the two weight-map partials of this row ----
+      float2* wp = S.wpart + (size_t)(tq & 1) * 2 * kT;   // double buffered
+      wp[grp * kT + row] = make_float2(ws, wc);
+      mbar_arrive(S.wbar);
+      if (!mbar_wait(S.wbar, tq & 1, abort_flag)) ok = false;
+      const float2 o = wp[(1 - grp) * kT + row];
+      const float W = (ws + o.x) + (wc + o.y);
+      // ---- wait for this tile's MMAs ----
+      if (!ok || !mbar_wait(S.dfull, tq & 1, abort_flag)) {
+        set_error(a.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      bool valid = user != 0xffffffffu;
+      if (valid && (int64_t)user >= a.P) {  // never expected: record and skip
+        set_error(a.err, ERR_INTERNAL);
+        valid = false;
+      }
+      const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
+      for (int cb = grp * half_cols; cb < (grp + 1) * half_cols; cb += 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem_d + lane_off + (uint32_t)cb));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!valid) continue;
+        const int c0 = c_base + cb;
+        if (a.mode == 2) {
+          float* dst = a.out + (size_t)user * a.C + c0;
+          if (c0 + 16 <= a.C && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              float4 v = make_float4(nch ? __uint_as_float(r[j]) * invW : invW,
+                                     nch ? __uint_as_float(r[j + 1]) * invW : invW,
+                                     nch ? __uint_as_float(r[j + 2]) * invW : invW,
+                                     nch ? __uint_as_float(r[j + 3]) * invW : invW);
+              *reinterpret_cast<float4*>(dst + j) = v;
+            }
+          } else {
+            for (int j = 0; j < 16 && c0 + j < a.C; ++j)
+              dst[j] = nch ? __uint_as_float(r[j]) * invW : invW;
+          }
+        } else {
+          float* dst = a.acc_num + (size_t)slot * a.C + c0;
+          for (int j = 0; j < 16 && c0 + j < a.C; ++j) {
+            const float v = nch ? __uint_as_float(r[j]) : 0.f;
+            dst[j] = (a.mode == 1) ? dst[j] + v : v;
+          }
+        }
+      }
+      if (valid && slab == 0 && grp == 0) {
+        if (a.mode == 2) {
+          if (a.out_w) a.out_w[user] = W;
+        } else {
+          float2 old = (a.mode == 1) ? a.acc_w[slot] : make_float2(0.f, 0.f);
+          const float t = old.x + W;
+          const float bp = t - old.x;
+          const float err = (old.x - (t - bp)) + (W - bp);
+          a.acc_w[slot] = make_float2(t, old.y + err);
+        }
+      }
+      fence_before();
+      mbar_arrive(S.dempty);
+    }
+    unsigned c = npair;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && c) atomicAdd(a.pairs, (unsigned long long)c);
+  }
+
+  // ---- teardown: all MMAs done before TMEM is released ----
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    int no_abort = 0;
+    if (!mbar_wait(S.fin, 0, &no_abort)) set_error(a.err, ERR_TIMEOUT);
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
+size_t smem_bytes(int cp, int ns) {
+  return (size_t)ns * cp * 64 + (size_t)ns * kK * (sizeof(float4) + sizeof(uint32_t)) +
+         (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (3 * kMaxStages + 4) * sizeof(uint64_t) +
+         16;
+}
+
+}  // namespace
+
+bool tc_supported(const cg_grid* g, int dtype, const void* data) {
+  return dtype == CG_BF16 && g->C % 8 == 0 && (reinterpret_cast<uintptr_t>(data) % 16) == 0;
+}
+
+cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
+                          int mode, float* out, float* out_w, int split) {
+  const Tiling& t = g->t128;
+  TcArgs a;
+  a.chi = t.chi;
+  a.clo = t.clo;
+  a.ta = t.a;
+  a.range_off = t.range_off;
+  a.range_s = t.range_s;
+  a.tile_cand = t.tile_cand;
+  a.n_tiles = t.n_tiles;
+  a.f1 = g->tgt_f1;
+  a.f2 = g->tgt_f2;
+  a.tll = g->tgt_ll;
+  a.perm_t = g->tgt_perm;
+  a.s_hi = g->s_hi;
+  a.s_lo = g->s_lo;
+  a.sperm = g->sorted_val;
+  a.lon = lon;
+  a.lat = lat;
+  a.data = static_cast<const __nv_bfloat16*>(data);
+  a.C = g->C;
+  const int slab = g->C < 256 ? g->C : 256;
+  a.cp = (slab + 31) / 32 * 32;
+  a.n_slabs = (g->C + a.cp - 1) / a.cp;
+  a.kd = g->kdev;
+  a.mode = mode;
+  a.acc_num = g->acc_num;
+  a.acc_w = g->acc_w;
+  a.out = out;
+  a.out_w = out_w;
+  a.P = g->P;
+  a.n_slots = g->n_slots;
+  a.pairs = g->d_pairs;
+  a.err = g->d_err;
+  // stages: as many as fit next to the accumulator in 512 TMEM columns
+  a.split = split ? 1 : 0;
+  int ns = 6;
+  if (a.cp <= 128) ns = 8;
+  const uint32_t acols = split ? 32u : 16u;
+  uint32_t need = (uint32_t)a.cp + acols * ns;
+  uint32_t cols = 32;
+  while (cols < need) cols <<= 1;
+  a.ns = ns;
+  a.tmem_cols = cols;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  size_t smem = smem_bytes(a.cp, ns);
+  // a CTA holding 512 TMEM columns must be alone on its SM: request enough
+  // shared memory that a second CTA cannot become resident
+  const int per_sm = (cols > 256) ? 1 : 2;
+  if (per_sm == 1 && smem < 120 * 1024) smem = 120 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t items = a.n_tiles * a.n_slabs;
+  int64_t grid = (int64_t)nsm * per_sm;
+  if (grid > items) grid = items;
+  if (grid < 1) return cudaSuccess;
+  k_grid_tc<<<(unsigned)grid, kThreads, smem, g->stream>>>(a);
+  g->n_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace cg

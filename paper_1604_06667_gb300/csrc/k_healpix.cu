@@ -151,7 +151,10 @@ __global__ void k_tile_query(const double4* __restrict__ tc64, int64_t n_tiles, 
     }
     const int sum = __shfl_sync(0xffffffffu, incl, 31);
     if (mode == 1) {
-      for (int q = 0; q < n; ++q) out[pos + incl - n + q] = rr[q];
+      for (int q = 0; q < n; ++q) {
+        rr[q].pad = (int32_t)tile;
+        out[pos + incl - n + q] = rr[q];
+      }
       pos += sum;
     }
     total += sum;
@@ -252,7 +255,8 @@ __device__ __forceinline__ int32_t lower_bound_u32(const uint32_t* __restrict__ 
 
 __global__ void k_sample_ranges(const Range* __restrict__ ranges, int64_t n_ranges,
                                 const int32_t* __restrict__ ring_off,
-                                const uint32_t* __restrict__ skey, int2* __restrict__ out) {
+                                const uint32_t* __restrict__ skey, int2* __restrict__ out,
+                                int32_t* __restrict__ tile_cand) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_ranges) return;
   const Range q = ranges[r];
@@ -263,6 +267,7 @@ __global__ void k_sample_ranges(const Range* __restrict__ ranges, int64_t n_rang
     hi = lower_bound_u32(skey, lo, b, (uint32_t)q.pix_hi + 1u);
   }
   out[r] = make_int2(lo, hi);
+  if (hi > lo) atomicAdd(&tile_cand[q.pad], hi - lo);
 }
 
 __global__ void k_export(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
@@ -294,19 +299,32 @@ cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int6
   return cudaGetLastError();
 }
 
-cudaError_t tiles_query(cg_grid* g) {
+void tiling_free(Tiling& t, cudaStream_t s) {
+  dfree(t.chi, s);
+  dfree(t.clo, s);
+  dfree(t.c64, s);
+  dfree(t.a, s);
+  dfree(t.tile_cand, s);
+  dfree(t.range_off, s);
+  dfree(t.ranges, s);
+  dfree(t.range_s, s);
+  t.n_ranges = 0;
+}
+
+cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   cudaStream_t s = g->stream;
-  const int64_t nt = g->n_tiles;
+  const int64_t nt = t.n_tiles;
   const double r = g->support_deg * kDeg2Rad;
   int64_t* counts = nullptr;
   cudaError_t e;
-  dfree(g->range_off, s);
-  dfree(g->ranges, s);
-  dfree(g->range_s, s);
+  dfree(t.range_off, s);
+  dfree(t.ranges, s);
+  dfree(t.range_s, s);
   if ((e = dalloc(&counts, (size_t)nt, s)) != cudaSuccess) return e;
   const int warps = 8;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(g->tile_c64, nt, g->nside, r, counts,
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, nt, g->nside, r, counts,
                                                         nullptr, nullptr, 0);
+  g->n_launches += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t* h = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt + 1));
   if (!h) return cudaErrorMemoryAllocation;
@@ -314,18 +332,19 @@ cudaError_t tiles_query(cg_grid* g) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { free(h); return e; }
   h[0] = 0;
-  for (int64_t t = 0; t < nt; ++t) h[t + 1] += h[t];
-  g->n_ranges = h[nt];
-  if ((e = dalloc(&g->range_off, (size_t)nt + 1, s)) != cudaSuccess) { free(h); return e; }
-  if ((e = dalloc(&g->ranges, (size_t)g->n_ranges, s)) != cudaSuccess) { free(h); return e; }
-  if ((e = dalloc(&g->range_s, (size_t)g->n_ranges, s)) != cudaSuccess) { free(h); return e; }
-  e = cudaMemcpyAsync(g->range_off, h, sizeof(int64_t) * (size_t)(nt + 1),
+  for (int64_t i = 0; i < nt; ++i) h[i + 1] += h[i];
+  t.n_ranges = h[nt];
+  if ((e = dalloc(&t.range_off, (size_t)nt + 1, s)) != cudaSuccess) { free(h); return e; }
+  if ((e = dalloc(&t.ranges, (size_t)t.n_ranges, s)) != cudaSuccess) { free(h); return e; }
+  if ((e = dalloc(&t.range_s, (size_t)t.n_ranges, s)) != cudaSuccess) { free(h); return e; }
+  e = cudaMemcpyAsync(t.range_off, h, sizeof(int64_t) * (size_t)(nt + 1),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   free(h);
   if (e != cudaSuccess) return e;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(g->tile_c64, nt, g->nside, r, nullptr,
-                                                        g->range_off, g->ranges, 1);
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, nt, g->nside, r, nullptr,
+                                                        t.range_off, t.ranges, 1);
+  g->n_launches += 1;
   dfree(counts, s);
   dfree(g->ring_off, s);
   if ((e = dalloc(&g->ring_off, (size_t)(4 * g->nside + 1), s)) != cudaSuccess) return e;
@@ -366,17 +385,19 @@ cudaError_t samples_sort(cg_grid* g, int64_t n) {
 }
 
 cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
-                            const float* weights, int64_t n) {
+                            const float* weights, int64_t n, Tiling& t) {
   cudaStream_t s = g->stream;
   const int64_t ns = g->nside;
   k_sample_gather<<<ceil_div(n, 256), 256, 0, s>>>(ns, g->sorted_key, g->sorted_val, lon, lat,
                                                    weights, n, g->s_hi, g->s_lo, g->d_err);
   k_ring_off<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, g->sorted_key, n, g->ring_off);
   g->n_launches += 2;
-  if (g->n_ranges > 0) {
-    k_sample_ranges<<<ceil_div(g->n_ranges, 256), 256, 0, s>>>(g->ranges, g->n_ranges,
-                                                               g->ring_off, g->sorted_key,
-                                                               g->range_s);
+  cudaError_t e = cudaMemsetAsync(t.tile_cand, 0, sizeof(int32_t) * (size_t)t.n_tiles, s);
+  if (e != cudaSuccess) return e;
+  if (t.n_ranges > 0) {
+    k_sample_ranges<<<ceil_div(t.n_ranges, 256), 256, 0, s>>>(t.ranges, t.n_ranges, g->ring_off,
+                                                              g->sorted_key, t.range_s,
+                                                              t.tile_cand);
     g->n_launches += 1;
   }
   g->last_n = n;

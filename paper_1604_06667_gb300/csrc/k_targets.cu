@@ -71,7 +71,7 @@ __global__ void k_node_bounds(const uint32_t* __restrict__ nid, int64_t P,
 // Child of every position (left part = a multiple of kTile targets) and the
 // bounding box of every child (order-preserving integer min / max).
 __global__ void k_node_split(const uint32_t* __restrict__ nid, const uint32_t* __restrict__ ord,
-                             const float4* __restrict__ pos, int64_t P,
+                             const float4* __restrict__ pos, int64_t P, uint32_t leaf,
                              const uint32_t* __restrict__ nstart,
                              const uint32_t* __restrict__ nend, uint32_t* __restrict__ child,
                              uint32_t* __restrict__ bmin, uint32_t* __restrict__ bmax) {
@@ -80,9 +80,9 @@ __global__ void k_node_split(const uint32_t* __restrict__ nid, const uint32_t* _
   const uint32_t n = nid[s];
   const uint32_t st = nstart[n], cnt = nend[n] - st;
   uint32_t c = 2u * n;
-  if (cnt > (uint32_t)kTile) {
-    const uint32_t m = (cnt + kTile - 1) / kTile;
-    const uint32_t left = (uint32_t)kTile * (m / 2);
+  if (cnt > leaf) {
+    const uint32_t m = (cnt + leaf - 1) / leaf;
+    const uint32_t left = leaf * (m / 2);
     if ((uint32_t)s - st >= left) c += 1u;
   }
   child[s] = c;
@@ -123,17 +123,19 @@ __global__ void k_node_unpack(const uint64_t* __restrict__ key, int64_t P,
   if (s < P) nid[s] = (uint32_t)(key[s] >> 32);
 }
 
-// One CTA of kTile threads per tile.
-__global__ void __launch_bounds__(kTile) k_tile_build(
+// One CTA of T threads per tile: centre, radius and tile-relative vectors.
+// The T = kTile2 build also writes the per-slot data shared by both tilings.
+template <int T>
+__global__ void __launch_bounds__(T) k_tile_build(
     const double* __restrict__ lon, const double* __restrict__ lat, int64_t P,
-    const uint32_t* __restrict__ order, uint32_t* __restrict__ tgt_perm,
-    float4* __restrict__ tile_chi, float4* __restrict__ tile_clo, double4* __restrict__ tile_c64,
-    float4* __restrict__ tgt_a, float4* __restrict__ tgt_e, float4* __restrict__ tgt_n,
+    const uint32_t* __restrict__ order, float4* __restrict__ tile_chi,
+    float4* __restrict__ tile_clo, double4* __restrict__ tile_c64, float4* __restrict__ tgt_a,
+    uint32_t* __restrict__ tgt_perm, float4* __restrict__ tgt_e, float4* __restrict__ tgt_n,
     double2* __restrict__ tgt_ll) {
-  __shared__ double red[3][kTile];
+  __shared__ double red[3][T];
   const int64_t tile = blockIdx.x;
   const int j = threadIdx.x;
-  const int64_t s = tile * kTile + j;
+  const int64_t s = tile * T + j;
   const bool valid = s < P;
   double x = 0, y = 0, z = 0, lo = 0, la = 0;
   uint32_t u = 0xffffffffu;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(kTile) k_tile_build(
   red[1][j] = y;
   red[2][j] = z;
   __syncthreads();
-  for (int o = kTile / 2; o > 0; o >>= 1) {
+  for (int o = T / 2; o > 0; o >>= 1) {
     if (j < o) {
       red[0][j] += red[0][j + o];
       red[1][j] += red[1][j + o];
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kTile) k_tile_build(
   double nrm = sqrt(cx * cx + cy * cy + cz * cz);
   __syncthreads();
   if (!(nrm > 1e-9)) {  // degenerate spread: use the first member
-    const uint32_t u0 = order[tile * kTile];
+    const uint32_t u0 = order[tile * T];
     unit_vec(lon[u0], lat[u0], cx, cy, cz);
     nrm = 1.0;
   }
@@ -174,26 +176,28 @@ __global__ void __launch_bounds__(kTile) k_tile_build(
   }
   red[0][j] = ang;
   __syncthreads();
-  for (int o = kTile / 2; o > 0; o >>= 1) {
+  for (int o = T / 2; o > 0; o >>= 1) {
     if (j < o) red[0][j] = fmax(red[0][j], red[0][j + o]);
     __syncthreads();
   }
   const double radius = red[0][0] * (1.0 + 1e-9) + 1e-12;
-  tgt_perm[s] = valid ? u : 0xffffffffu;
-  if (valid) {
-    tgt_a[s] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
-    double sl, cl, sb, cb;
-    sincos(lo * kDeg2Rad, &sl, &cl);
-    sincos(la * kDeg2Rad, &sb, &cb);
-    tgt_e[s] = make_float4((float)(-sl), (float)cl, 0.f, 0.f);
-    tgt_n[s] = make_float4((float)(-sb * cl), (float)(-sb * sl), (float)cb, 0.f);
-    tgt_ll[s] = make_double2(lo, la);
-  } else {
-    // an empty slot sits far outside every support radius
-    tgt_a[s] = make_float4(4.f, 4.f, 4.f, 0.f);
-    tgt_e[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-    tgt_n[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-    tgt_ll[s] = make_double2(0.0, 0.0);
+  // an empty slot sits far outside every support radius
+  tgt_a[s] = valid ? make_float4((float)dx, (float)dy, (float)dz, 0.f)
+                   : make_float4(4.f, 4.f, 4.f, 0.f);
+  if (tgt_perm) {
+    tgt_perm[s] = valid ? u : 0xffffffffu;
+    if (valid) {
+      double sl, cl, sb, cb;
+      sincos(lo * kDeg2Rad, &sl, &cl);
+      sincos(la * kDeg2Rad, &sb, &cb);
+      tgt_e[s] = make_float4((float)(-sl), (float)cl, 0.f, 0.f);
+      tgt_n[s] = make_float4((float)(-sb * cl), (float)(-sb * sl), (float)cb, 0.f);
+      tgt_ll[s] = make_double2(lo, la);
+    } else {
+      tgt_e[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      tgt_n[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      tgt_ll[s] = make_double2(0.0, 0.0);
+    }
   }
   if (j == 0) {
     float hx, lx, hy, ly, hz, lz;
@@ -219,26 +223,38 @@ __global__ void k_set_axes(const float4* __restrict__ e, const float4* __restric
 
 }  // namespace
 
+static cudaError_t tiling_alloc(Tiling& t, int T, int64_t P, cudaStream_t s) {
+  t.T = T;
+  t.n_tiles = (P + T - 1) / T;
+  cudaError_t e;
+  if ((e = dalloc(&t.chi, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&t.clo, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&t.c64, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&t.a, (size_t)(t.n_tiles * T), s)) != cudaSuccess) return e;
+  if ((e = dalloc(&t.tile_cand, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
 cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
   cudaStream_t s = g->stream;
   const int64_t P = g->P;
-  g->n_tiles = (P + kTile - 1) / kTile;
-  const int64_t slots = g->n_tiles * kTile;
   cudaError_t e;
+  if ((e = tiling_alloc(g->t64, kTile, P, s)) != cudaSuccess) return e;
+  if ((e = tiling_alloc(g->t128, kTile2, P, s)) != cudaSuccess) return e;
+  g->n_slots = g->t128.n_tiles * kTile2;
+  const int64_t slots = g->n_slots;
   if ((e = dalloc(&g->tgt_perm, slots, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->tile_chi, g->n_tiles, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->tile_clo, g->n_tiles, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->tile_c64, g->n_tiles, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->tgt_a, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_e, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_n, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_f1, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_f2, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_ll, slots, s)) != cudaSuccess) return e;
 
-  // levels of the k-d tree: each level halves the number of tiles per node
-  int levels = 0;
-  while (((int64_t)1 << levels) < (int64_t)g->n_tiles) ++levels;
+  // k-d tree levels: leaves of kTile2 targets, then one more level that splits
+  // every leaf into two kTile halves (so the 128-tiles are sibling pairs)
+  int levels2 = 0;
+  while (((int64_t)1 << levels2) < g->t128.n_tiles) ++levels2;
+  const int levels = levels2 + 1;
   const int64_t max_nodes = (int64_t)1 << (levels + 1);
   float4* pos = nullptr;
   uint32_t *ord = nullptr, *nid = nullptr, *child = nullptr, *val = nullptr;
@@ -261,12 +277,13 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
     g->n_launches += 1;
   }
   for (int l = 0; l < levels && e == cudaSuccess; ++l) {
+    const uint32_t leaf = (l < levels2) ? (uint32_t)kTile2 : (uint32_t)kTile;
     const int64_t nchild = (int64_t)1 << (l + 1);
     e = cudaMemsetAsync(bmin, 0xff, sizeof(uint32_t) * (size_t)(3 * nchild), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bmax, 0x00, sizeof(uint32_t) * (size_t)(3 * nchild), s);
     if (e != cudaSuccess) break;
     k_node_bounds<<<nb, 256, 0, s>>>(nid, P, nstart, nend);
-    k_node_split<<<nb, 256, 0, s>>>(nid, ord, pos, P, nstart, nend, child, bmin, bmax);
+    k_node_split<<<nb, 256, 0, s>>>(nid, ord, pos, P, leaf, nstart, nend, child, bmin, bmax);
     k_node_keys<<<nb, 256, 0, s>>>(child, ord, pos, P, bmin, bmax, key, val);
     g->n_launches += 3;
     uint64_t* sk = nullptr;
@@ -281,10 +298,13 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
                                        cudaMemcpyDeviceToDevice, s);
   }
   if (e == cudaSuccess) {
-    k_tile_build<<<(unsigned)g->n_tiles, kTile, 0, s>>>(
-        lon, lat, P, ord, g->tgt_perm, g->tile_chi, g->tile_clo, g->tile_c64, g->tgt_a, g->tgt_e,
-        g->tgt_n, g->tgt_ll);
-    g->n_launches += 1;
+    k_tile_build<kTile2><<<(unsigned)g->t128.n_tiles, kTile2, 0, s>>>(
+        lon, lat, P, ord, g->t128.chi, g->t128.clo, g->t128.c64, g->t128.a, g->tgt_perm,
+        g->tgt_e, g->tgt_n, g->tgt_ll);
+    k_tile_build<kTile><<<(unsigned)g->t64.n_tiles, kTile, 0, s>>>(
+        lon, lat, P, ord, g->t64.chi, g->t64.clo, g->t64.c64, g->t64.a, nullptr, nullptr,
+        nullptr, nullptr);
+    g->n_launches += 2;
     e = cudaGetLastError();
   }
   if (w.keys_alt) cudaFreeAsync(w.keys_alt, s);
@@ -305,7 +325,7 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
 }
 
 cudaError_t targets_set_axes(cg_grid* g, double pa_deg) {
-  const int64_t slots = g->n_tiles * kTile;
+  const int64_t slots = g->n_slots;
   const double pa = pa_deg * kDeg2Rad;
   k_set_axes<<<ceil_div(slots, 256), 256, 0, g->stream>>>(g->tgt_e, g->tgt_n, g->tgt_f1,
                                                           g->tgt_f2, slots, (float)cos(pa),

@@ -202,3 +202,20 @@ def test_bad_arguments():
         g.set_kernel("gauss1d", (0.1,), 0.0, 0.01)
     g.set_kernel("gauss1d", (0.1,), 0.3, 0.05)
     g.close()
+
+
+def test_stage_timing_and_destroy():
+    """Stage timing on, several calls, read, destroy: events are owned once."""
+    import torch
+    from paper_1604_06667_gb300 import Gridder
+    wl = workloads.random_field(350, 2000, 16, 4, 10.0, 10.0, 1.0, 2.0 * ARCMIN)
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=4)
+    g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
+    g.set_timing(True)
+    for rep in range(3):
+        for _ in range(3):
+            g.grid_oneshot(wl.lon_s, wl.lat_s, torch.from_numpy(wl.data))
+        t = g.read_timing()
+        assert t["grid_launches"] == 3 and t["grid"] > 0 and t["sort"] > 0
+    g.grid(wl.lon_s, wl.lat_s, torch.from_numpy(wl.data))
+    g.close()

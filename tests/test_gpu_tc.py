@@ -1,0 +1,161 @@
+"""Tensor-core form (BF16 tcgen05, FP32 accumulation in TMEM) against the FP64
+oracle run on the same BF16-rounded channel data (paper Eq. 1-3).
+
+CG_PATH_TC stores each weight as a hi + lo pair of BF16 numbers (~16
+significant bits); with FP32 accumulation the only difference from the FP64
+definition on the same BF16 data is rounding, bound TC_TOL on the
+S-normalised map error and the relative weight-map error.  CG_PATH_TC_FAST
+keeps single BF16 weights (8 significant bits); W is summed from the same
+rounded weights, so R stays a weighted mean and the error is at most
+2^-8 of S (bound FAST_TOL).
+Also checked: the fused one-shot epilogue, store / add accumulation, several
+adds, the channel-major layout, ragged channel counts (padding to the MMA N),
+more than 256 channels (several channel slabs), the elliptical kernel and
+sample weights, and agreement with the FP32 CUDA-core form.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import compare_maps, gpu_kernel_args, kernel_of
+
+pytestmark = pytest.mark.gpu
+
+TC_TOL = 5e-5
+FAST_TOL = 2.0 ** -8
+BF16_TOL = TC_TOL
+ARCMIN = 1.0 / 60.0
+
+
+def bf16_data(wl):
+    import torch
+    d16 = torch.from_numpy(wl.data).to(torch.bfloat16)
+    return d16, d16.to(torch.float32).numpy()
+
+
+def oracle_ref(wl, data):
+    ns = oracle.nside_for_resolution(wl.hpx_maxres)
+    om = None if wl.omega is None else wl.omega.astype(np.float64)
+    return oracle.grid_lookup(ns, wl.lon_t, wl.lat_t, wl.lon_s, wl.lat_s,
+                              data.astype(np.float64), kernel_of(wl), om)
+
+
+def gridder(wl, path=None):
+    from paper_1604_06667_gb300 import Gridder, _capi
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=wl.n_channels)
+    kt, kp = gpu_kernel_args(wl)
+    g.set_kernel(kt, kp, wl.support, wl.hpx_maxres)
+    g.set_path(_capi.CG_PATH_TC if path is None else path)
+    return g
+
+
+def oneshot(wl, d16, path=None, channel_major=False):
+    import torch
+    g = gridder(wl, path)
+    w = torch.empty(wl.n_targets, device="cuda")
+    out = g.grid_oneshot(wl.lon_s, wl.lat_s, d16,
+                         None if wl.omega is None else wl.omega, out_weights=w,
+                         channel_major=channel_major)
+    g.sync()
+    info = g.info()
+    res = out.cpu().numpy(), w.cpu().numpy(), info
+    g.close()
+    return res
+
+
+def test_cube_small_oneshot_fused():
+    from paper_1604_06667_gb300 import _capi
+    wl = workloads.cube(scale=0.004)
+    d16, dr = bf16_data(wl)
+    out, w, info = oneshot(wl, d16)
+    assert info["path"] == _capi.CG_PATH_TC and info["tile_size"] == 128
+    ref = oracle_ref(wl, dr)
+    me, mw = compare_maps(out, w, ref, tol=BF16_TOL, wtol=BF16_TOL)
+    assert info["n_pairs"] == ref.npairs
+    print("cube small: map err %.2e, weight err %.2e" % (me, mw))
+
+
+@pytest.mark.parametrize("C", [8, 24, 64, 200, 256, 264, 512])
+def test_channel_counts_tc(C):
+    wl = workloads.random_field(400 + C, 1500, 25, C, 33.0, 12.0, 1.2, 2.0 * ARCMIN)
+    d16, dr = bf16_data(wl)
+    out, w, _ = oneshot(wl, d16)
+    compare_maps(out, w, oracle_ref(wl, dr), tol=BF16_TOL, wtol=BF16_TOL)
+
+
+def test_accumulate_modes_and_layout():
+    import torch
+    wl = workloads.random_field(450, 4000, 30, 32, 250.0, -45.0, 1.5, 2.5 * ARCMIN, weights=True)
+    d16, dr = bf16_data(wl)
+    ref = oracle_ref(wl, dr)
+    g = gridder(wl)
+    cuts = [0, 1000, 2500, 4000]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        g.grid(wl.lon_s[a:b], wl.lat_s[a:b], d16[a:b], wl.omega[a:b])
+    w = torch.empty(wl.n_targets, device="cuda")
+    out = g.get_datacube(out_weights=w)
+    compare_maps(out.cpu().numpy(), w.cpu().numpy(), ref, tol=BF16_TOL, wtol=BF16_TOL)
+    # finalize is non-destructive; channel-major layout
+    out2 = g.get_datacube(channel_major=True)
+    compare_maps(out2.cpu().numpy().T, w.cpu().numpy(), ref, tol=BF16_TOL, wtol=BF16_TOL)
+    g.close()
+    out3, w3, _ = oneshot(wl, d16, channel_major=True)
+    compare_maps(out3.T, w3, ref, tol=BF16_TOL, wtol=BF16_TOL)
+
+
+def test_elliptical_tc():
+    wl = workloads.allsky(scale=0.004, n_channels=16)
+    wl.kernel = {"type": "gauss2d", "smaj": 1.5, "smin": 0.9, "pa": 30.0}
+    wl.support = 4.5
+    wl.hpx_maxres = 0.45
+    d16, dr = bf16_data(wl)
+    out, w, _ = oneshot(wl, d16)
+    compare_maps(out, w, oracle_ref(wl, dr), tol=BF16_TOL, wtol=BF16_TOL)
+
+
+def test_tc_agrees_with_fp32_form():
+    from paper_1604_06667_gb300 import _capi
+    wl = workloads.random_field(460, 3000, 28, 64, 100.0, 60.0, 1.2, 2.0 * ARCMIN)
+    d16, dr = bf16_data(wl)
+    a, wa, ia = oneshot(wl, d16, path=_capi.CG_PATH_TC)
+    b, wb, ib = oneshot(wl, d16, path=_capi.CG_PATH_FP32)
+    assert ia["path"] == _capi.CG_PATH_TC and ib["path"] == _capi.CG_PATH_FP32
+    assert ia["n_pairs"] == ib["n_pairs"]
+    ref = oracle_ref(wl, dr)
+    compare_maps(b, wb, ref)                              # FP32 form: 1e-5
+    compare_maps(a, wa, ref, tol=BF16_TOL, wtol=BF16_TOL)  # BF16 form
+
+
+def test_fast_form_bound():
+    from paper_1604_06667_gb300 import _capi
+    wl = workloads.allsky(scale=0.004, n_channels=16)
+    wl.kernel = {"type": "gauss2d", "smaj": 1.5, "smin": 0.9, "pa": 30.0}
+    wl.support = 4.5
+    wl.hpx_maxres = 0.45
+    d16, dr = bf16_data(wl)
+    out, w, info = oneshot(wl, d16, path=_capi.CG_PATH_TC_FAST)
+    assert info["path"] == _capi.CG_PATH_TC_FAST
+    me, mw = compare_maps(out, w, oracle_ref(wl, dr), tol=FAST_TOL, wtol=FAST_TOL)
+    print("fast form: map err %.2e, weight err %.2e" % (me, mw))
+
+
+def test_persistent_multi_tile_per_cta():
+    """More tiles than resident CTAs: each persistent CTA runs several tiles
+    (pipeline phases carried across tiles)."""
+    wl = workloads.cube(scale=0.12, n_channels=32)
+    d16, dr = bf16_data(wl)
+    out, w, info = oneshot(wl, d16)
+    assert info["n_tiles"] > 2 * 152
+    compare_maps(out, w, oracle_ref(wl, dr), tol=BF16_TOL, wtol=BF16_TOL)
+
+
+def test_tc_rejects_unsupported_inputs():
+    import torch
+    from paper_1604_06667_gb300 import _capi
+    wl = workloads.random_field(470, 200, 8, 6, 10.0, 10.0, 0.5, 2.0 * ARCMIN)
+    g = gridder(wl)
+    with pytest.raises(_capi.CygridError) as ei:
+        g.grid(wl.lon_s, wl.lat_s, torch.from_numpy(wl.data))    # FP32 data, C % 8 != 0
+    assert ei.value.status == _capi.CG_EINVAL
+    g.close()

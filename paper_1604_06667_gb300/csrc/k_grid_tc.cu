@@ -22,9 +22,12 @@
 //   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 and
 //              candidates 16 (w / 4) .. + 15 of every chunk; weight-map sums
 //              from the same BF16-rounded weights the MMA consumes; epilogue;
-//   warp 8     producer: walks the tile's sample ranges, writes tile-relative
-//              candidate vectors and stages data rows with cp.async;
-//   warp 9     MMA issue (one lane) and tcgen05.commit.
+//   warps 8-9  producers (alternate chunks): walk the tile's sample ranges,
+//              write tile-relative candidate vectors and stage data rows with
+//              cp.async (each instruction covers 8 rows x 4 channel blocks, so
+//              shared-memory writes are at most 4-way conflicted while every
+//              row segment read from global memory is 64 contiguous bytes);
+//   warp 10    MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
 #include <cuda_bf16.h>
@@ -38,9 +41,10 @@ namespace {
 constexpr int kT = kTile2;          // targets per tile = MMA M
 constexpr int kK = 32;              // candidates per chunk
 constexpr int kWW = 8;              // weight warps
-constexpr int kThreads = (kWW + 2) * 32;
-constexpr int kProdWarp = kWW;
-constexpr int kMmaWarp = kWW + 1;
+constexpr int kNP = 2;              // producer warps (alternate chunks)
+constexpr int kThreads = (kWW + kNP + 1) * 32;
+constexpr int kProdWarp = kWW;      // first producer warp
+constexpr int kMmaWarp = kWW + kNP;
 constexpr int kMaxStages = 8;
 // a wait gives up after ~1 s of SM clock (or at once after another role gave up)
 constexpr long long kWaitCycles = 2000000000LL;
@@ -166,6 +170,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
                : "memory");
 }
 
+template <int KT, bool SPLIT, bool BIG>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int ns = a.ns;
@@ -217,13 +222,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
   fence_after();
   const uint32_t tmem = *S.tmem_base;
   const uint32_t tmem_d = tmem;              // columns [0, cp)
-  const uint32_t acols = a.split ? 32u : 16u;   // TMEM columns of A per stage
+  const uint32_t acols = SPLIT ? 32u : 16u;     // TMEM columns of A per stage
   const uint32_t tmem_a = tmem + (uint32_t)cp;  // columns [cp, cp + acols ns)
   const int64_t n_items = a.n_tiles * a.n_slabs;
   volatile int* abort_flag = S.abort_flag;
 
-  if (warp == kProdWarp) {
-    // ------------------------------------------------------------ producer
+  if (warp >= kProdWarp && warp < kProdWarp + kNP) {
+    // ------------------------------------------------------------ producers
+    const int pw = warp - kProdWarp;
     uint32_t q = 0;
     const uint32_t piece_per_row = (uint32_t)cp / 8;
     for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
@@ -239,7 +245,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
       int2 wrange = make_int2(0, 0);
       for (int ch = 0; ch < nch; ++ch, ++q) {
         const int st = (int)(q % (uint32_t)ns);
-        if (q >= (uint32_t)ns) {
+        const bool mine = (ch % kNP) == pw;   // every producer walks all chunks
+        if (mine && q >= (uint32_t)ns) {
           if (!mbar_wait(&S.empty[st], ((q / ns) - 1) & 1, abort_flag)) {
             set_error(a.err, ERR_TIMEOUT);
             *abort_flag = 1;
@@ -271,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
             off = 0;
           }
         }
+        if (!mine) continue;
         // padding candidate: far from every target and from the empty-slot
         // sentinel (4, 4, 4) of the tile-relative target vectors
         float4 cb = make_float4(-4.f, -4.f, -4.f, 0.f);
@@ -287,9 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
         __syncwarp();
         // data rows -> B stage (MN-major core matrices)
         const uint32_t bbase = su32(S.B + (size_t)st * cp * 64);
-        const uint32_t npieces = (uint32_t)kK * piece_per_row;
-        for (uint32_t pc = lane; pc < npieces; pc += 32) {
-          const uint32_t k = pc / piece_per_row, nb = pc % piece_per_row;
+        // instruction it: rows 8 (it / G) .. + 7 and channel blocks 4 (it % G) .. + 3,
+        // with G = piece_per_row / 4; lane -> (row lane % 8, block lane / 8)
+        const uint32_t G = piece_per_row / 4;
+        const uint32_t n_it = (kK / 8) * G;
+        const uint32_t k_in = lane & 7u, nb_in = lane >> 3;
+        for (uint32_t it = 0; it < n_it; ++it) {
+          const uint32_t k = (it / G) * 8 + k_in;
+          const uint32_t nb = (it % G) * 4 + nb_in;
           const uint32_t rid = S.cidx[st * kK + k];
           const int c0 = c_base + (int)nb * 8;
           const bool ok = (rid != 0xffffffffu) && (c0 < a.C);
@@ -333,10 +346,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             const uint64_t bd = smem_desc(bstage + kk * 256u, 128u, 512u);
-            const int halves = a.split ? 2 : 1;
-            for (int h = 0; h < halves; ++h) {
+#pragma unroll
+            for (int h = 0; h < (SPLIT ? 2 : 1); ++h) {
               // A of candidates 16 kk .. 16 kk + 15: hi at +0, lo at +8 columns
-              const uint32_t at = tmem_a + st * acols + (uint32_t)(kk * (a.split ? 16 : 8) + h * 8);
+              const uint32_t at = tmem_a + st * acols + (uint32_t)(kk * (SPLIT ? 16 : 8) + h * 8);
               const uint32_t acc = (ch > 0 || kk > 0 || h > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -372,6 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
     const int grp = warp >> 2;                // candidate half
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     const int half_cols = cp / 2;             // epilogue columns of this group
+    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f), q3 = a.kd.k1 * (1.f / 90.f);
+    const float q4 = a.kd.k2;
+    const float c2_in = a.kd.c2_in, c2_out = a.kd.c2_out;
     uint32_t q = 0, tq = 0;
     unsigned npair = 0;
     for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
       if (slot >= a.n_slots) set_error(a.err, ERR_INTERNAL);
       const float4 at = a.ta[slot];
       float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
-      if (a.kd.type == CG_GAUSS2D) {
+      if (KT == CG_GAUSS2D) {
         f1 = a.f1[slot];
         f2 = a.f2[slot];
       }
@@ -396,62 +412,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
           ok = false;
           break;
         }
+        // ---- 16 weights of this thread's row, branch-free ----
+        float w[16];
+        uint32_t band = 0;     // pairs whose cut needs the FP64 decision
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float4 cb = S.cand[st * kK + grp * 16 + k];
+          const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
+          const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          float e;
+          if (BIG) {
+            const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+            const float d2 = d * d;
+            if (KT == CG_GAUSS1D) {
+              e = q1 * d2;
+            } else {
+              const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+              const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+              const float s2 = fmaf(ap, ap, bp * bp);
+              const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+              e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+            }
+          } else if (KT == CG_GAUSS1D) {
+            // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent
+            e = c2 * fmaf(c2, fmaf(c2, q3, q2), q1);
+          } else {
+            // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
+            const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+            const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+            const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
+            e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+          }
+          const float wk = ex2_approx(e) * cb.w;
+          const bool in = c2 <= c2_out;
+          w[k] = in ? wk : 0.f;
+          npair += (in && slab == 0) ? 1u : 0u;
+          band |= (in && c2 >= c2_in) ? (1u << k) : 0u;
+        }
+        // rare: decide pairs inside the guard band from the FP64 coordinates
+        if (__any_sync(0xffffffffu, band != 0u)) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            if (band & (1u << k)) {
+              const uint32_t idx = S.cidx[st * kK + grp * 16 + k];
+              const double2 tl = a.tll[slot];
+              const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+              if (!(d <= a.kd.r_rad)) {
+                w[k] = 0.f;
+                if (slab == 0) --npair;
+              }
+            }
+          }
+        }
         uint32_t packed[8], packed_lo[8];
         float part = 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float wpair[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = grp * 16 + 2 * j + h;
-            const float4 cb = S.cand[st * kK + k];
-            const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
-            const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float w = 0.f;
-            if (c2 <= a.kd.c2_out) {
-              float d2;
-              if (!a.kd.big_support) {
-                d2 = c2 * fmaf(c2, fmaf(c2, 1.f / 90.f, 1.f / 12.f), 1.f);
-              } else {
-                const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
-                d2 = d * d;
-              }
-              float ex;
-              if (a.kd.type == CG_GAUSS1D) {
-                ex = a.kd.k1 * d2;
-              } else {
-                const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-                const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-                const float s2 = fmaf(ap, ap, bp * bp);
-                const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
-                ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
-              }
-              w = ex2_approx(ex) * cb.w;
-              bool inside = true;
-              if (c2 >= a.kd.c2_in) {
-                const uint32_t idx = S.cidx[st * kK + k];
-                const double2 tl = a.tll[slot];
-                const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
-                inside = d <= a.kd.r_rad;
-              }
-              if (!inside) w = 0.f;
-              else if (slab == 0) ++npair;
-            }
-            wpair[h] = w;
-          }
-          const __nv_bfloat162 b2 = __floats2bfloat162_rn(wpair[0], wpair[1]);
-          const float2 back = __bfloat1622float2(b2);
-          packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
-          if (a.split) {
-            // w_lo = w - w_hi; the weight map sums the weights the MMAs see
-            const __nv_bfloat162 l2 =
-                __floats2bfloat162_rn(wpair[0] - back.x, wpair[1] - back.y);
-            const float2 lback = __bfloat1622float2(l2);
+          part += w[2 * j] + w[2 * j + 1];
+          if (SPLIT) {
+            // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
+            // truncation), w_lo = w - w_hi is exact in FP32, then rounded
+            const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
+            const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
+            packed[j] = __byte_perm(u0, u1, 0x7632);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
+                                                            w[2 * j + 1] - __uint_as_float(u1));
             packed_lo[j] = *reinterpret_cast<const uint32_t*>(&l2);
-            part += (back.x + lback.x) + (back.y + lback.y);
           } else {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
+            packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
             packed_lo[j] = 0u;
-            part += back.x + back.y;
           }
         }
         // Kahan accumulation of the chunk partial into the weight map
@@ -461,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
           wc = (t - ws) - y;
           ws = t;
         }
-        if (a.split) {
+        if (SPLIT) {
           const uint32_t ta_addr = tmem_a + lane_off + st * acols + (uint32_t)(grp * 16);
           asm volatile(
               "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -571,6 +601,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
   }
 }
 
+using KernFn = void (*)(TcArgs);
+KernFn pick_kernel(int kt, bool split, bool big) {
+  if (kt == CG_GAUSS1D) {
+    if (big) return split ? k_grid_tc<CG_GAUSS1D, true, true> : k_grid_tc<CG_GAUSS1D, false, true>;
+    return split ? k_grid_tc<CG_GAUSS1D, true, false> : k_grid_tc<CG_GAUSS1D, false, false>;
+  }
+  if (big) return split ? k_grid_tc<CG_GAUSS2D, true, true> : k_grid_tc<CG_GAUSS2D, false, true>;
+  return split ? k_grid_tc<CG_GAUSS2D, true, false> : k_grid_tc<CG_GAUSS2D, false, false>;
+}
+
 size_t smem_bytes(int cp, int ns) {
   return (size_t)ns * cp * 64 + (size_t)ns * kK * (sizeof(float4) + sizeof(uint32_t)) +
          (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (3 * kMaxStages + 4) * sizeof(uint64_t) +
@@ -636,14 +676,15 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   // shared memory that a second CTA cannot become resident
   const int per_sm = (cols > 256) ? 1 : 2;
   if (per_sm == 1 && smem < 120 * 1024) smem = 120 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   const int64_t items = a.n_tiles * a.n_slabs;
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) return cudaSuccess;
-  k_grid_tc<<<(unsigned)grid, kThreads, smem, g->stream>>>(a);
+  auto kern = pick_kernel(a.kd.type, split != 0, a.kd.big_support != 0);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kThreads, smem, g->stream>>>(a);
   g->n_launches += 1;
   return cudaGetLastError();
 }

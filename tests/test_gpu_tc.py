@@ -143,10 +143,10 @@ def test_fast_form_bound():
 def test_persistent_multi_tile_per_cta():
     """More tiles than resident CTAs: each persistent CTA runs several tiles
     (pipeline phases carried across tiles)."""
-    wl = workloads.cube(scale=0.12, n_channels=32)
+    wl = workloads.cube(scale=0.2, n_channels=32)
     d16, dr = bf16_data(wl)
     out, w, info = oneshot(wl, d16)
-    assert info["n_tiles"] > 2 * 152
+    assert info["n_tiles"] > 2 * 152   # at least two tiles per persistent CTA
     compare_maps(out, w, oracle_ref(wl, dr), tol=BF16_TOL, wtol=BF16_TOL)
 
 

@@ -13,23 +13,26 @@
 // the target row, so the weights never touch shared memory).  In the default
 // (split) form every weight is stored as w_hi + w_lo, two BF16 numbers
 // (~16 significant bits), and each K step issues one MMA per half against
-// the same B; the fast form keeps only w_hi (8 significant bits).  B is staged in
-// shared memory in the MN-major, unswizzled canonical layout (8 channels x
-// 8 candidates per 128-byte core matrix; LBO = 128 B between candidate
-// blocks, SBO = 512 B between channel blocks).
+// the same B; the fast form keeps only w_hi (8 significant bits).  B is
+// gathered from the caller's [N][C] data straight into shared memory by the
+// Tensor Memory Accelerator: one cp.async.bulk.tensor tile::gather4 moves four
+// arbitrary sample rows x 64 channels with 128-byte swizzling, which is the
+// MN-major SW128 canonical layout of the MMA (atoms of 8 candidates x 64
+// channels; LBO = 4 KB between channel blocks, SBO = 1 KB between candidate
+// groups).  Padding candidates point past the last row and arrive as zeros.
 //
 // Warp roles (persistent CTA, static round-robin over (tile, slab) items):
 //   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 and
 //              candidates 16 (w / 4) .. + 15 of every chunk; weight-map sums
 //              from the same BF16-rounded weights the MMA consumes; epilogue;
-//   warps 8-9  producers (alternate chunks): walk the tile's sample ranges,
-//              write tile-relative candidate vectors and stage data rows with
-//              cp.async (each instruction covers 8 rows x 4 channel blocks, so
-//              shared-memory writes are at most 4-way conflicted while every
-//              row segment read from global memory is 64 contiguous bytes);
-//   warp 10    MMA issue (one lane) and tcgen05.commit.
+//   warps 8-11 producers (every fourth chunk each): walk the tile's sample
+//              ranges, write tile-relative candidate vectors, issue the TMA
+//              gathers of the chunk's data rows;
+//   warp 12    MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "cg_common.cuh"
@@ -41,7 +44,7 @@ namespace {
 constexpr int kT = kTile2;          // targets per tile = MMA M
 constexpr int kK = 32;              // candidates per chunk
 constexpr int kWW = 8;              // weight warps
-constexpr int kNP = 2;              // producer warps (alternate chunks)
+constexpr int kNP = 4;              // producer warps (chunk q goes to warp q % kNP)
 constexpr int kThreads = (kWW + kNP + 1) * 32;
 constexpr int kProdWarp = kWW;      // first producer warp
 constexpr int kMmaWarp = kWW + kNP;
@@ -68,7 +71,7 @@ struct TcArgs {
   const double* lat;
   const __nv_bfloat16* data;
   int C;
-  int cp;        // padded channels per slab (multiple of 32, <= 256)
+  int cp;        // padded channels per slab (multiple of 64, <= 256)
   int n_slabs;
   int ns;        // pipeline stages
   int split;     // 1: weights as hi + lo BF16 pairs (two MMAs per K step)
@@ -79,6 +82,7 @@ struct TcArgs {
   float2* acc_w;
   float* out;
   float* out_w;
+  int n_rows;    // samples (rows of the data tensor)
   int64_t P;
   int64_t n_slots;
   unsigned long long* pairs;
@@ -164,14 +168,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-               "r"(src_bytes)
-               : "memory");
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(addr, lbo, sbo) | ((uint64_t)2 << 61);  // layout: 128-byte swizzle
 }
 
 template <int KT, bool SPLIT, bool BIG>
-__global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ CUtensorMap tmap,
+                                                         TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int ns = a.ns;
   const int cp = a.cp;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
   }
   if (tid == 32) {
     for (int s = 0; s < ns; ++s) {
-      mbar_init(&S.full[s], 64);        // 32 staging stores + 32 cp.async completions
+      mbar_init(&S.full[s], 32);        // producer lanes (+ TMA transaction bytes)
       mbar_init(&S.afull[s], kWW * 32);  // every weight thread
       mbar_init(&S.empty[s], 1);        // MMA commit
     }
@@ -231,7 +234,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
     // ------------------------------------------------------------ producers
     const int pw = warp - kProdWarp;
     uint32_t q = 0;
-    const uint32_t piece_per_row = (uint32_t)cp / 8;
     for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
       const int64_t tile = item / a.n_slabs;
       const int c_base = (int)(item % a.n_slabs) * cp;
@@ -293,27 +295,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
         S.cand[st * kK + lane] = cb;
         S.cidx[st * kK + lane] = idx;
         __syncwarp();
-        // data rows -> B stage (MN-major core matrices)
+        // data rows -> B stage: TMA gather4 of 4 rows x 64 channels per lane
         const uint32_t bbase = su32(S.B + (size_t)st * cp * 64);
-        // instruction it: rows 8 (it / G) .. + 7 and channel blocks 4 (it % G) .. + 3,
-        // with G = piece_per_row / 4; lane -> (row lane % 8, block lane / 8)
-        const uint32_t G = piece_per_row / 4;
-        const uint32_t n_it = (kK / 8) * G;
-        const uint32_t k_in = lane & 7u, nb_in = lane >> 3;
-        for (uint32_t it = 0; it < n_it; ++it) {
-          const uint32_t k = (it / G) * 8 + k_in;
-          const uint32_t nb = (it % G) * 4 + nb_in;
-          const uint32_t rid = S.cidx[st * kK + k];
-          const int c0 = c_base + (int)nb * 8;
-          const bool ok = (rid != 0xffffffffu) && (c0 < a.C);
-          const __nv_bfloat16* src = ok ? a.data + (size_t)rid * a.C + c0 : a.data;
-          const uint32_t dst = bbase + nb * 512u + (k >> 3) * 128u + (k & 7u) * 16u;
-          cp_async16(dst, src, ok ? 16u : 0u);
+        const int nblk = cp / 64;                 // 64-channel blocks
+        const uint32_t bytes = (uint32_t)kK * (uint32_t)cp * 2u;
+        const int row_pad = a.n_rows;             // past the end: zero rows
+        int rowk[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t rid = __shfl_sync(0xffffffffu, idx, (lane & 7) * 4 + t);
+          rowk[t] = (rid == 0xffffffffu) ? row_pad : (int)rid;
         }
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                         su32(&S.full[st]))
-                     : "memory");
-        mbar_arrive(&S.full[st]);
+        if (lane == 0)
+          asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                           su32(&S.full[st])),
+                       "r"(bytes)
+                       : "memory");
+        __syncwarp();
+        if (lane < nblk * 8) {
+          const int j = lane >> 3, h = lane & 7;  // channel block, row quad
+          const uint32_t dst = bbase + (uint32_t)j * 4096u + (uint32_t)(h >> 1) * 1024u +
+                               (uint32_t)(h & 1) * 512u;
+          const int x = c_base + 64 * j;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(rowk[0]), "r"(rowk[1]),
+              "r"(rowk[2]), "r"(rowk[3]), "r"(su32(&S.full[st]))
+              : "memory");
+        }
+        if (lane != 0) mbar_arrive(&S.full[st]);
       }
     }
   } else if (warp == kMmaWarp) {
@@ -341,11 +352,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
             break;
           }
           fence_after();
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           const uint32_t bstage = su32(S.B + (size_t)st * cp * 64);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t bd = smem_desc(bstage + kk * 256u, 128u, 512u);
+            // SW128 MN-major: 8-candidate groups 1 KB apart, 64-channel blocks 4 KB apart
+            const uint64_t bd = smem_desc_sw128(bstage + kk * 2048u, 4096u, 1024u);
 #pragma unroll
             for (int h = 0; h < (SPLIT ? 2 : 1); ++h) {
               // A of candidates 16 kk .. 16 kk + 15: hi at +0, lo at +8 columns
@@ -601,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(TcArgs a) {
   }
 }
 
-using KernFn = void (*)(TcArgs);
+using KernFn = void (*)(const CUtensorMap, TcArgs);
 KernFn pick_kernel(int kt, bool split, bool big) {
   if (kt == CG_GAUSS1D) {
     if (big) return split ? k_grid_tc<CG_GAUSS1D, true, true> : k_grid_tc<CG_GAUSS1D, false, true>;
@@ -621,6 +632,20 @@ size_t smem_bytes(int cp, int ns) {
 
 bool tc_supported(const cg_grid* g, int dtype, const void* data) {
   return dtype == CG_BF16 && g->C % 8 == 0 && (reinterpret_cast<uintptr_t>(data) % 16) == 0;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
 }
 
 cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
@@ -646,7 +671,7 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.data = static_cast<const __nv_bfloat16*>(data);
   a.C = g->C;
   const int slab = g->C < 256 ? g->C : 256;
-  a.cp = (slab + 31) / 32 * 32;
+  a.cp = (slab + 63) / 64 * 64;
   a.n_slabs = (g->C + a.cp - 1) / a.cp;
   a.kd = g->kdev;
   a.mode = mode;
@@ -654,14 +679,20 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.acc_w = g->acc_w;
   a.out = out;
   a.out_w = out_w;
+  a.n_rows = (int)g->last_n;
   a.P = g->P;
   a.n_slots = g->n_slots;
   a.pairs = g->d_pairs;
   a.err = g->d_err;
-  // stages: as many as fit next to the accumulator in 512 TMEM columns
+  // Stages: chunk q uses stage q % ns and is staged by producer warp q % kNP.
+  // ns must be a multiple of kNP so that every stage always belongs to the
+  // same producer warp: the parity-based empty-barrier wait is only valid
+  // while its waiter is at most one phase ahead, which a second producer
+  // racing through the same stage could break.  8 stages of split weights
+  // (32 TMEM columns each) plus a 256-column accumulator fill 512 columns.
   a.split = split ? 1 : 0;
-  int ns = 6;
-  if (a.cp <= 128) ns = 8;
+  const int ns = 8;
+  static_assert(8 % kNP == 0, "stages must be a multiple of the producer warps");
   const uint32_t acols = split ? 32u : 16u;
   uint32_t need = (uint32_t)a.cp + acols * ns;
   uint32_t cols = 32;
@@ -680,11 +711,24 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) return cudaSuccess;
+  // tensor map over the caller's [N][C] BF16 rows: 64-channel x 1-row boxes,
+  // 128-byte swizzle (the layout of the MMA's B operand); rows past N read 0
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)g->C, (cuuint64_t)g->last_n};
+  const cuuint64_t gstride[1] = {(cuuint64_t)g->C * 2};
+  const cuuint32_t box[2] = {64, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(data), gdim, gstride, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   auto kern = pick_kernel(a.kd.type, split != 0, a.kd.big_support != 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)grid, kThreads, smem, g->stream>>>(a);
+  kern<<<(unsigned)grid, kThreads, smem, g->stream>>>(tmap, a);
   g->n_launches += 1;
   return cudaGetLastError();
 }

@@ -205,6 +205,34 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
 cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
                                int64_t* ring_off, int64_t n);
 
+/* No-allocation variant of the sample index (RING keys + stable sort).
+ *
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory -- code that runs under a fixed, pre-reserved
+ * memory budget (the allocator may not be touched after start-up), inside
+ * another framework's memory manager that forbids foreign allocations, or on a
+ * hot path where an allocation could block or fail.  It computes what
+ * cg_grid_add followed by cg_grid_export_index computes for the samples' index:
+ *   sorted_pix  device [n] int64: RING indices at `nside`, ascending; samples
+ *               with non-finite or out-of-range coordinates get 12 nside^2 and
+ *               sort to the end (they are not reported as errors here);
+ *   perm        device [n] int64: original index of each sorted entry, ties in
+ *               ascending original order (a stable sort).
+ * All scratch lives in one static device array of the library
+ * (CG_NOALLOC_MAX_SAMPLES samples, about 4.3 MB), which every GPU that loads
+ * the library holds until the process exits.  n above CG_NOALLOC_MAX_SAMPLES
+ * returns CG_EINVAL.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array, so calls that overlap on the GPU (different streams, or
+ * different host threads) race: order them on one stream.  The array keeps
+ * the previous call's contents; the call clears what must start at zero.
+ * Asynchronous on `stream`; nside 1 .. 8192. */
+#define CG_NOALLOC_MAX_SAMPLES 262144
+cg_status cg_sort_samples_noalloc(int32_t nside, const double* lon_deg, const double* lat_deg,
+                                  int64_t n, int64_t* sorted_pix, int64_t* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

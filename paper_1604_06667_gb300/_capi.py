@@ -60,7 +60,10 @@ SIGNATURES = {
     "cg_grid_export_index": [_vp, _vp, _vp, _vp, _i64],
     "cg_set_timing": [_vp, _i32],
     "cg_read_timing": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)],
+    "cg_sort_samples_noalloc": [_i32, _vp, _vp, _i64, _vp, _vp, _vp],
 }
+
+CG_NOALLOC_MAX_SAMPLES = 262144
 
 _lib = None
 
@@ -113,6 +116,7 @@ cg_ang2pix_ring = _call("cg_ang2pix_ring")
 cg_grid_export_index = _call("cg_grid_export_index")
 cg_set_timing = _call("cg_set_timing")
 cg_read_timing = _call("cg_read_timing")
+cg_sort_samples_noalloc = _call("cg_sort_samples_noalloc")
 
 
 def cg_last_error() -> str:

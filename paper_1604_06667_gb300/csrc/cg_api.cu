@@ -454,4 +454,21 @@ cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
   return CG_OK;
 }
 
+cg_status cg_sort_samples_noalloc(int32_t nside, const double* lon_deg, const double* lat_deg,
+                                  int64_t n, int64_t* sorted_pix, int64_t* perm, void* stream) {
+  g_last_error.clear();
+  if (nside < 1 || nside > 8192)
+    return fail(CG_EINVAL, "cg_sort_samples_noalloc: nside must be in [1, 8192]");
+  if (n < 0 || n > CG_NOALLOC_MAX_SAMPLES)
+    return fail(CG_EINVAL,
+                "cg_sort_samples_noalloc: n = %lld exceeds the no-allocation limit of %d samples",
+                (long long)n, CG_NOALLOC_MAX_SAMPLES);
+  if (n > 0 && (!lon_deg || !lat_deg || !sorted_pix || !perm))
+    return fail(CG_EINVAL, "cg_sort_samples_noalloc: null pointer");
+  CG_CUDA(sort_samples_noalloc(nside, lon_deg, lat_deg, n, sorted_pix, perm,
+                               static_cast<cudaStream_t>(stream)),
+          "cg_sort_samples_noalloc");
+  return CG_OK;
+}
+
 }  // extern "C"

@@ -127,6 +127,10 @@ namespace cg {
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
                            SortWork& w, cudaStream_t s, uint32_t** out_keys,
                            uint32_t** out_vals);
+cudaError_t radix_sort_u32_scratch(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                                   uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist,
+                                   uint32_t* totals, cudaStream_t s, uint32_t** out_keys,
+                                   uint32_t** out_vals);
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
                            SortWork& w, cudaStream_t s, uint64_t** out_keys,
                            uint32_t** out_vals);
@@ -156,6 +160,9 @@ cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double
 bool tc_supported(const cg_grid* g, int dtype, const void* data);
 cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
                           int mode, float* out, float* out_w, int split);
+// k_noalloc.cu -- sample index on the library's static scratch array.
+cudaError_t sort_samples_noalloc(int nside, const double* lon, const double* lat, int64_t n,
+                                 int64_t* sorted_pix, int64_t* perm, cudaStream_t s);
 // k_finalize.cu -- normalisation and output layout.
 cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w);
 

@@ -223,6 +223,31 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bi
   return radix_sort_impl<uint32_t>(keys, vals, n, key_bits, w, s, out_keys, out_vals);
 }
 
+// Same passes as radix_sort_u32 on caller-provided scratch (no allocation):
+// keys_alt / vals_alt hold n entries, hist 256 * ceil(n / 4096), totals 256.
+cudaError_t radix_sort_u32_scratch(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                                   uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* hist,
+                                   uint32_t* totals, cudaStream_t s, uint32_t** out_keys,
+                                   uint32_t** out_vals) {
+  *out_keys = keys;
+  *out_vals = vals;
+  if (n <= 0) return cudaSuccess;
+  const int nblk = (int)ceil_div(n, kTileKeys);
+  uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    cudaError_t e = cudaMemsetAsync(totals, 0, kRadix * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_hist<uint32_t><<<nblk, kThreads, 0, s>>>(kin, n, shift, hist, totals, nblk);
+    k_scan<<<kRadix, kThreads, 0, s>>>(hist, totals, nblk);
+    k_scatter<uint32_t><<<nblk, kThreads, 0, s>>>(kin, vin, kout, vout, n, shift, hist, nblk);
+    uint32_t* tk = kin; kin = kout; kout = tk;
+    uint32_t* tv = vin; vin = vout; vout = tv;
+  }
+  *out_keys = kin;
+  *out_vals = vin;
+  return cudaGetLastError();
+}
+
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
                            SortWork& w, cudaStream_t s, uint64_t** out_keys,
                            uint32_t** out_vals) {

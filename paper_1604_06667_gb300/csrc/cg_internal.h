@@ -50,6 +50,11 @@ struct Tiling {           // geometry of one tiling of the targets
   Range* ranges = nullptr;        // [n_ranges]
   int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi) of the last add
   int32_t* tile_cand = nullptr;   // [n_tiles] candidates per tile of the last add
+  // 128-target tiles only: the four 32-target quarters (one TMEM lane quarter
+  // each; k-d leaves), FP64 centre + radius, and the centre relative to the
+  // tile centre in FP32 with the radius as a chord
+  double4* sub64 = nullptr;       // [n_tiles * 4]
+  float4* subf = nullptr;         // [n_tiles * 4]
 };
 
 struct SortWork {         // radix-sort scratch

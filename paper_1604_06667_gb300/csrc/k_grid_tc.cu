@@ -22,13 +22,16 @@
 // groups).  Padding candidates point past the last row and arrive as zeros.
 //
 // Warp roles (persistent CTA, static round-robin over (tile, slab) items):
-//   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 and
-//              candidates 16 (w / 4) .. + 15 of every chunk; weight-map sums
-//              from the same BF16-rounded weights the MMA consumes; epilogue;
-//   warps 8-11 producers (every fourth chunk each): walk the tile's sample
+//   warps 0-15 weights: warp w handles target rows 32 (w % 4) .. + 31 (one
+//              TMEM lane quarter, a compact 32-target k-d leaf) and candidates
+//              8 (w / 4) .. + 7 of every chunk; a group of 8 candidates that
+//              cannot reach the quarter (disc of radius quarter radius + r) is
+//              skipped; weight-map sums from the weights the MMA consumes;
+//              epilogue (the quarter's columns split four ways);
+//   warps 16-19 producers (every fourth chunk each): walk the tile's sample
 //              ranges, write tile-relative candidate vectors, issue the TMA
 //              gathers of the chunk's data rows;
-//   warp 12    MMA issue (one lane) and tcgen05.commit.
+//   warp 20    MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
 #include <cuda.h>
@@ -43,7 +46,7 @@ namespace {
 
 constexpr int kT = kTile2;          // targets per tile = MMA M
 constexpr int kK = 32;              // candidates per chunk
-constexpr int kWW = 8;              // weight warps
+constexpr int kWW = 16;             // weight warps (4 per TMEM lane quarter)
 constexpr int kNP = 4;              // producer warps (chunk q goes to warp q % kNP)
 constexpr int kThreads = (kWW + kNP + 1) * 32;
 constexpr int kProdWarp = kWW;      // first producer warp
@@ -56,6 +59,7 @@ struct TcArgs {
   const float4* chi;
   const float4* clo;
   const float4* ta;
+  const float4* subf;   // per tile x quarter: centre rel. to the tile centre, chord radius
   const int64_t* range_off;
   const int2* range_s;
   const int32_t* tile_cand;
@@ -93,7 +97,7 @@ struct Smem {
   uint8_t* B;          // ns stages of cp * 64 bytes
   float4* cand;        // ns x kK
   uint32_t* cidx;      // ns x kK
-  float2* wpart;       // 2 buffers x kWW/4 x kT partial weight sums
+  float2* wpart;       // 2 buffers x (kWW / 4) groups x kT partial weight sums
   uint64_t* full;      // ns
   uint64_t* afull;     // ns
   uint64_t* empty;     // ns
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     S.cidx = reinterpret_cast<uint32_t*>(p);
     p += (size_t)ns * kK * sizeof(uint32_t);
     S.wpart = reinterpret_cast<float2*>(p);
-    p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);
+    p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);  // (unchanged formula, kWW = 16)
     S.full = reinterpret_cast<uint64_t*>(p);
     S.afull = S.full + kMaxStages;
     S.empty = S.afull + kMaxStages;
@@ -392,10 +396,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     }
   } else {
     // ------------------------------------------------------------ weights
-    const int row = (warp & 3) * 32 + lane;   // TMEM lane = target row
-    const int grp = warp >> 2;                // candidate half
-    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    const int half_cols = cp / 2;             // epilogue columns of this group
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;      // TMEM lane = target row
+    const int grp = warp >> 2;                // candidates 8 grp .. 8 grp + 7
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int part_cols = cp / 4;             // epilogue columns of this group
+    const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
     const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f), q3 = a.kd.k1 * (1.f / 90.f);
     const float q4 = a.kd.k2;
     const float c2_in = a.kd.c2_in, c2_out = a.kd.c2_out;
@@ -415,6 +421,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       }
       const uint32_t user = a.perm_t[slot];
       const int nch = (a.tile_cand[tile] + kK - 1) / kK;
+      // the quarter's reach: candidates beyond (quarter radius + r) give w = 0
+      const float4 sq = a.subf[tile * 4 + quarter];
+      const float reach2 = (rc + sq.w) * (rc + sq.w) * 1.0001f + 1e-12f;
       float ws = 0.f, wc = 0.f;
       bool ok = true;
       for (int ch = 0; ch < nch; ++ch, ++q) {
@@ -423,62 +432,75 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           ok = false;
           break;
         }
-        // ---- 16 weights of this thread's row, branch-free ----
-        float w[16];
+        // ---- 8 weights of this thread's row, branch-free ----
+        const int kb = st * kK + grp * 8;
+        bool reach = false;
+        if (lane < 8) {
+          const float4 cb = S.cand[kb + lane];
+          const float ex = cb.x - sq.x, ey = cb.y - sq.y, ez = cb.z - sq.z;
+          reach = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= reach2;
+        }
+        const bool grp_live = __any_sync(0xffffffffu, reach);
+        float w[8];
         uint32_t band = 0;     // pairs whose cut needs the FP64 decision
+        if (grp_live) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float4 cb = S.cand[st * kK + grp * 16 + k];
-          const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
-          const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          float e;
-          if (BIG) {
-            const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
-            const float d2 = d * d;
-            if (KT == CG_GAUSS1D) {
-              e = q1 * d2;
+          for (int k = 0; k < 8; ++k) {
+            const float4 cb = S.cand[kb + k];
+            const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
+            const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float e;
+            if (BIG) {
+              const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+              const float d2 = d * d;
+              if (KT == CG_GAUSS1D) {
+                e = q1 * d2;
+              } else {
+                const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+                const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+                const float s2 = fmaf(ap, ap, bp * bp);
+                const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+                e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+              }
+            } else if (KT == CG_GAUSS1D) {
+              // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent
+              e = c2 * fmaf(c2, fmaf(c2, q3, q2), q1);
             } else {
+              // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
               const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
               const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-              const float s2 = fmaf(ap, ap, bp * bp);
-              const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+              const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
               e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
             }
-          } else if (KT == CG_GAUSS1D) {
-            // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent
-            e = c2 * fmaf(c2, fmaf(c2, q3, q2), q1);
-          } else {
-            // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
-            const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-            const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-            const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
-            e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+            const float wk = ex2_approx(e) * cb.w;
+            const bool in = c2 <= c2_out;
+            w[k] = in ? wk : 0.f;
+            npair += (in && slab == 0) ? 1u : 0u;
+            band |= (in && c2 >= c2_in) ? (1u << k) : 0u;
           }
-          const float wk = ex2_approx(e) * cb.w;
-          const bool in = c2 <= c2_out;
-          w[k] = in ? wk : 0.f;
-          npair += (in && slab == 0) ? 1u : 0u;
-          band |= (in && c2 >= c2_in) ? (1u << k) : 0u;
-        }
-        // rare: decide pairs inside the guard band from the FP64 coordinates
-        if (__any_sync(0xffffffffu, band != 0u)) {
+          // rare: decide pairs inside the guard band from the FP64 coordinates
+          if (__any_sync(0xffffffffu, band != 0u)) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            if (band & (1u << k)) {
-              const uint32_t idx = S.cidx[st * kK + grp * 16 + k];
-              const double2 tl = a.tll[slot];
-              const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
-              if (!(d <= a.kd.r_rad)) {
-                w[k] = 0.f;
-                if (slab == 0) --npair;
+            for (int k = 0; k < 8; ++k) {
+              if (band & (1u << k)) {
+                const uint32_t idx = S.cidx[kb + k];
+                const double2 tl = a.tll[slot];
+                const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+                if (!(d <= a.kd.r_rad)) {
+                  w[k] = 0.f;
+                  if (slab == 0) --npair;
+                }
               }
             }
           }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) w[k] = 0.f;
         }
-        uint32_t packed[8], packed_lo[8];
+        uint32_t packed[4], packed_lo[4];
         float part = 0.f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
           part += w[2 * j] + w[2 * j + 1];
           if (SPLIT) {
             // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
@@ -502,36 +524,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           wc = (t - ws) - y;
           ws = t;
         }
-        if (SPLIT) {
-          const uint32_t ta_addr = tmem_a + lane_off + st * acols + (uint32_t)(grp * 16);
-          asm volatile(
-              "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-              "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta_addr),
-              "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3]), "r"(packed[4]),
-              "r"(packed[5]), "r"(packed[6]), "r"(packed[7]), "r"(packed_lo[0]),
-              "r"(packed_lo[1]), "r"(packed_lo[2]), "r"(packed_lo[3]), "r"(packed_lo[4]),
-              "r"(packed_lo[5]), "r"(packed_lo[6]), "r"(packed_lo[7])
-              : "memory");
-        } else {
-          const uint32_t ta_addr = tmem_a + lane_off + st * acols + (uint32_t)(grp * 8);
-          asm volatile(
-              "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
-                  ta_addr),
-              "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3]), "r"(packed[4]),
-              "r"(packed[5]), "r"(packed[6]), "r"(packed[7])
-              : "memory");
+        {
+          // candidates 8 grp .. 8 grp + 7 = K step grp / 2, half grp % 2:
+          // split: hi at columns 16 (grp / 2) + 4 (grp % 2), lo 8 further
+          const uint32_t col = SPLIT ? (uint32_t)((grp >> 1) * 16 + (grp & 1) * 4)
+                                     : (uint32_t)((grp >> 1) * 8 + (grp & 1) * 4);
+          const uint32_t ta_addr = tmem_a + lane_off + st * acols + col;
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta_addr),
+                       "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3])
+                       : "memory");
+          if (SPLIT)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(
+                             ta_addr + 8u),
+                         "r"(packed_lo[0]), "r"(packed_lo[1]), "r"(packed_lo[2]),
+                         "r"(packed_lo[3])
+                         : "memory");
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
         mbar_arrive(&S.afull[st]);
       }
       // ---- epilogue: combine the two weight-map partials of this row ----
-      float2* wp = S.wpart + (size_t)(tq & 1) * 2 * kT;   // double buffered
+      constexpr int kGroups = kWW / 4;
+      float2* wp = S.wpart + (size_t)(tq & 1) * kGroups * kT;   // double buffered
       wp[grp * kT + row] = make_float2(ws, wc);
       mbar_arrive(S.wbar);
       if (!mbar_wait(S.wbar, tq & 1, abort_flag)) ok = false;
-      const float2 o = wp[(1 - grp) * kT + row];
-      const float W = (ws + o.x) + (wc + o.y);
+      float W = 0.f;
+#pragma unroll
+      for (int g2 = 0; g2 < kGroups; ++g2) {
+        const float2 o = wp[g2 * kT + row];
+        W += o.x + o.y;
+      }
       // ---- wait for this tile's MMAs ----
       if (!ok || !mbar_wait(S.dfull, tq & 1, abort_flag)) {
         set_error(a.err, ERR_TIMEOUT);
@@ -545,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         valid = false;
       }
       const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
-      for (int cb = grp * half_cols; cb < (grp + 1) * half_cols; cb += 16) {
+      for (int cb = grp * part_cols; cb < (grp + 1) * part_cols; cb += 16) {
         uint32_t r[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -655,6 +679,7 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.chi = t.chi;
   a.clo = t.clo;
   a.ta = t.a;
+  a.subf = t.subf;
   a.range_off = t.range_off;
   a.range_s = t.range_s;
   a.tile_cand = t.tile_cand;

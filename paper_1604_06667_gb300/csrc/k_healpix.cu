@@ -86,19 +86,43 @@ __device__ double disc_halfwidth(double tc, double R, double ta, double tb) {
   return acos(xmin);
 }
 
-// Pixel ranges of ring i met by the disc; writes up to 2 into out (if given).
-__device__ int ring_ranges(int64_t ns, int64_t i, double tc, double pc, double R,
-                           Range* out) {
-  const double hw = disc_halfwidth(tc, R, ring_colat(ns, i - 1), ring_colat(ns, i + 1));
-  if (hw < 0.0) return 0;
+// A disc on the sphere: colatitude, longitude (radians) and radius.
+struct Disc {
+  double tc, pc, R;
+};
+
+// Pixel ranges of ring i met by the union of nd discs (the hull of their
+// pixel intervals on the ring, a superset); writes up to 2 into out.
+__device__ int ring_ranges(int64_t ns, int64_t i, const Disc* discs, int nd, Range* out) {
   const RingGeo g = ring_geo(ns, i);
   const double dphi = 2.0 * kPi / (double)g.count;
-  const double W = hw + 0.5 * dphi + 1e-12;
+  const double ta = ring_colat(ns, i - 1), tb = ring_colat(ns, i + 1);
+  bool any = false, full = false;
+  double lo = 0.0, hi = 0.0;   // hull of [pc - W, pc + W], unwrapped near the first disc
+  for (int q = 0; q < nd && !full; ++q) {
+    const double hw = disc_halfwidth(discs[q].tc, discs[q].R, ta, tb);
+    if (hw < 0.0) continue;
+    const double W = hw + 0.5 * dphi + 1e-12;
+    if (W >= kPi) { full = true; break; }
+    double c = discs[q].pc;
+    if (any) {  // move c to within pi of the hull's first centre
+      const double ref = 0.5 * (lo + hi);
+      while (c - ref > kPi) c -= 2.0 * kPi;
+      while (ref - c > kPi) c += 2.0 * kPi;
+      lo = fmin(lo, c - W);
+      hi = fmax(hi, c + W);
+    } else {
+      lo = c - W;
+      hi = c + W;
+      any = true;
+    }
+  }
+  if (!any && !full) return 0;
   int64_t jlo = 0, jhi = g.count - 1;
-  bool full = W >= kPi;
+  if (!full && hi - lo >= 2.0 * kPi) full = true;
   if (!full) {
-    jlo = (int64_t)ceil((pc - W) / dphi - g.phase);
-    jhi = (int64_t)floor((pc + W) / dphi - g.phase);
+    jlo = (int64_t)ceil(lo / dphi - g.phase);
+    jhi = (int64_t)floor(hi / dphi - g.phase);
     if (jhi < jlo) return 0;
     if (jhi - jlo + 1 >= g.count) full = true;
   }
@@ -120,19 +144,38 @@ __device__ int ring_ranges(int64_t ns, int64_t i, double tc, double pc, double R
   return 2;
 }
 
-// One warp per tile; mode 0 counts ranges, mode 1 writes them.
-__global__ void k_tile_query(const double4* __restrict__ tc64, int64_t n_tiles, int64_t ns,
+__device__ __forceinline__ Disc make_disc(double4 c, double r_rad) {
+  Disc d;
+  d.tc = acos(fmin(1.0, fmax(-1.0, c.z)));
+  d.pc = atan2(c.y, c.x);
+  d.R = c.w + r_rad;
+  return d;
+}
+
+// One warp per tile; mode 0 counts ranges, mode 1 writes them.  With sub64
+// the tile's candidates are those of its four quarter discs (tighter than one
+// disc around the tile centre); otherwise one disc of radius (tile radius + r).
+__global__ void k_tile_query(const double4* __restrict__ tc64,
+                             const double4* __restrict__ sub64, int64_t n_tiles, int64_t ns,
                              double r_rad, int64_t* __restrict__ counts,
                              const int64_t* __restrict__ offs, Range* __restrict__ out,
                              int mode) {
   const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (tile >= n_tiles) return;
-  const double4 c = tc64[tile];
-  const double R = c.w + r_rad;
-  const double tcol = acos(fmin(1.0, fmax(-1.0, c.z)));
-  const double pc = atan2(c.y, c.x);
-  const double tlo = fmax(0.0, tcol - R), thi = fmin(kPi, tcol + R);
+  Disc discs[4];
+  int nd = 1;
+  discs[0] = make_disc(tc64[tile], r_rad);
+  if (sub64) {
+    nd = 4;
+    for (int q = 0; q < 4; ++q) discs[q] = make_disc(sub64[tile * 4 + q], r_rad);
+  }
+  // colatitude span of all discs
+  double tlo = kPi, thi = 0.0;
+  for (int q = 0; q < nd; ++q) {
+    tlo = fmin(tlo, fmax(0.0, discs[q].tc - discs[q].R));
+    thi = fmax(thi, fmin(kPi, discs[q].tc + discs[q].R));
+  }
   int64_t ilo = (int64_t)floor(ring_coord(ns, cos(tlo))) - 2;
   int64_t ihi = (int64_t)ceil(ring_coord(ns, cos(thi))) + 2;
   ilo = ilo < 1 ? 1 : ilo;
@@ -142,7 +185,7 @@ __global__ void k_tile_query(const double4* __restrict__ tc64, int64_t n_tiles, 
   for (int64_t base = ilo; base <= ihi; base += 32) {
     const int64_t i = base + lane;
     Range rr[2];
-    const int n = (i <= ihi) ? ring_ranges(ns, i, tcol, pc, R, rr) : 0;
+    const int n = (i <= ihi) ? ring_ranges(ns, i, discs, nd, rr) : 0;
     int incl = n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -305,6 +348,8 @@ void tiling_free(Tiling& t, cudaStream_t s) {
   dfree(t.c64, s);
   dfree(t.a, s);
   dfree(t.tile_cand, s);
+  dfree(t.sub64, s);
+  dfree(t.subf, s);
   dfree(t.range_off, s);
   dfree(t.ranges, s);
   dfree(t.range_s, s);
@@ -322,8 +367,8 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   dfree(t.range_s, s);
   if ((e = dalloc(&counts, (size_t)nt, s)) != cudaSuccess) return e;
   const int warps = 8;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, nt, g->nside, r, counts,
-                                                        nullptr, nullptr, 0);
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, t.sub64, nt, g->nside, r,
+                                                        counts, nullptr, nullptr, 0);
   g->n_launches += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t* h = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt + 1));
@@ -342,8 +387,8 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   free(h);
   if (e != cudaSuccess) return e;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, nt, g->nside, r, nullptr,
-                                                        t.range_off, t.ranges, 1);
+  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, t.sub64, nt, g->nside, r,
+                                                        nullptr, t.range_off, t.ranges, 1);
   g->n_launches += 1;
   dfree(counts, s);
   dfree(g->ring_off, s);

@@ -4,8 +4,11 @@
 // lines (Sect. 3.5, WcsGrid / SlGrid).  Here targets are always a list of
 // directions.  To give each CTA a compact group of targets (its "tile"), the
 // targets are split by a k-d tree over their unit vectors: every node is cut
-// along its widest axis at a multiple of kTile targets, so all leaves hold
-// exactly kTile targets (except the last) and each leaf is a compact box.
+// along its widest axis at a multiple of the leaf size, so all leaves hold
+// exactly that many targets (except the last) and each leaf is a compact box.
+// The tree is cut to 128-target leaves, then each leaf into 64 + 64 and each
+// of those into 32 + 32, so a 128-tile is two 64-tiles and four 32-target
+// quarters, all compact.
 // The tree is built level by level with one stable 64-bit radix sort per
 // level keyed by (child node, coordinate along the child's widest axis).
 // Each tile stores
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(T) k_tile_build(
     const uint32_t* __restrict__ order, float4* __restrict__ tile_chi,
     float4* __restrict__ tile_clo, double4* __restrict__ tile_c64, float4* __restrict__ tgt_a,
     uint32_t* __restrict__ tgt_perm, float4* __restrict__ tgt_e, float4* __restrict__ tgt_n,
-    double2* __restrict__ tgt_ll) {
+    double2* __restrict__ tgt_ll, double4* __restrict__ sub64, float4* __restrict__ subf) {
   __shared__ double red[3][T];
   const int64_t tile = blockIdx.x;
   const int j = threadIdx.x;
@@ -199,6 +202,35 @@ __global__ void __launch_bounds__(T) k_tile_build(
       tgt_ll[s] = make_double2(0.0, 0.0);
     }
   }
+  if (sub64) {
+    // 32-target quarters: warp-level centroid and radius (empty slots ignored)
+    double sx = x, sy = y, sz = z;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    double qn = sqrt(sx * sx + sy * sy + sz * sz);
+    if (!(qn > 1e-9)) {  // empty or degenerate quarter: use the tile centre
+      sx = cx; sy = cy; sz = cz; qn = 1.0;
+    }
+    sx /= qn; sy /= qn; sz /= qn;
+    double qa = 0.0;
+    if (valid) {
+      const double ex = x - sx, ey = y - sy, ez = z - sz;
+      qa = 2.0 * asin(fmin(1.0, 0.5 * sqrt(ex * ex + ey * ey + ez * ez)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qa = fmax(qa, __shfl_xor_sync(0xffffffffu, qa, o));
+    qa = qa * (1.0 + 1e-9) + 1e-12;
+    if ((j & 31) == 0) {
+      const int64_t qi = tile * (T / 32) + (j >> 5);
+      sub64[qi] = make_double4(sx, sy, sz, qa);
+      subf[qi] = make_float4((float)(sx - cx), (float)(sy - cy), (float)(sz - cz),
+                             (float)(2.0 * sin(0.5 * qa)));
+    }
+  }
   if (j == 0) {
     float hx, lx, hy, ly, hz, lz;
     split_f64(cx, hx, lx);
@@ -232,6 +264,10 @@ static cudaError_t tiling_alloc(Tiling& t, int T, int64_t P, cudaStream_t s) {
   if ((e = dalloc(&t.c64, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
   if ((e = dalloc(&t.a, (size_t)(t.n_tiles * T), s)) != cudaSuccess) return e;
   if ((e = dalloc(&t.tile_cand, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  if (T == kTile2) {
+    if ((e = dalloc(&t.sub64, (size_t)(t.n_tiles * 4), s)) != cudaSuccess) return e;
+    if ((e = dalloc(&t.subf, (size_t)(t.n_tiles * 4), s)) != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -250,11 +286,11 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
   if ((e = dalloc(&g->tgt_f2, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_ll, slots, s)) != cudaSuccess) return e;
 
-  // k-d tree levels: leaves of kTile2 targets, then one more level that splits
-  // every leaf into two kTile halves (so the 128-tiles are sibling pairs)
+  // k-d tree levels: leaves of kTile2 targets, then two more levels that split
+  // every leaf into kTile halves and those into 32-target quarters
   int levels2 = 0;
   while (((int64_t)1 << levels2) < g->t128.n_tiles) ++levels2;
-  const int levels = levels2 + 1;
+  const int levels = levels2 + 2;
   const int64_t max_nodes = (int64_t)1 << (levels + 1);
   float4* pos = nullptr;
   uint32_t *ord = nullptr, *nid = nullptr, *child = nullptr, *val = nullptr;
@@ -277,7 +313,8 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
     g->n_launches += 1;
   }
   for (int l = 0; l < levels && e == cudaSuccess; ++l) {
-    const uint32_t leaf = (l < levels2) ? (uint32_t)kTile2 : (uint32_t)kTile;
+    const uint32_t leaf =
+        (l < levels2) ? (uint32_t)kTile2 : (l == levels2 ? (uint32_t)kTile : 32u);
     const int64_t nchild = (int64_t)1 << (l + 1);
     e = cudaMemsetAsync(bmin, 0xff, sizeof(uint32_t) * (size_t)(3 * nchild), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bmax, 0x00, sizeof(uint32_t) * (size_t)(3 * nchild), s);
@@ -300,10 +337,10 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
   if (e == cudaSuccess) {
     k_tile_build<kTile2><<<(unsigned)g->t128.n_tiles, kTile2, 0, s>>>(
         lon, lat, P, ord, g->t128.chi, g->t128.clo, g->t128.c64, g->t128.a, g->tgt_perm,
-        g->tgt_e, g->tgt_n, g->tgt_ll);
+        g->tgt_e, g->tgt_n, g->tgt_ll, g->t128.sub64, g->t128.subf);
     k_tile_build<kTile><<<(unsigned)g->t64.n_tiles, kTile, 0, s>>>(
         lon, lat, P, ord, g->t64.chi, g->t64.clo, g->t64.c64, g->t64.a, nullptr, nullptr,
-        nullptr, nullptr);
+        nullptr, nullptr, nullptr, nullptr);
     g->n_launches += 2;
     e = cudaGetLastError();
   }

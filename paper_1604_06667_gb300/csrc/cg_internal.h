@@ -49,6 +49,7 @@ struct Tiling {           // geometry of one tiling of the targets
   int64_t* range_off = nullptr;   // [n_tiles + 1]
   Range* ranges = nullptr;        // [n_ranges]
   int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi) of the last add
+  int32_t* range_c = nullptr;     // [n_ranges] the tile's candidates before each range
   int32_t* tile_cand = nullptr;   // [n_tiles] candidates per tile of the last add
   // 128-target tiles only: the four 32-target quarters (one TMEM lane quarter
   // each; k-d leaves), FP64 centre + radius, and the centre relative to the

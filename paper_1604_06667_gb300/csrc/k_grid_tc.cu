@@ -13,30 +13,38 @@
 // the target row, so the weights never touch shared memory).  In the default
 // (split) form every weight is stored as w_hi + w_lo, two BF16 numbers
 // (~16 significant bits), and each K step issues one MMA per half against
-// the same B; the fast form keeps only w_hi (8 significant bits).  B is
-// gathered from the caller's [N][C] data straight into shared memory by the
-// Tensor Memory Accelerator: one cp.async.bulk.tensor tile::gather4 moves four
-// arbitrary sample rows x 64 channels with 128-byte swizzling, which is the
-// MN-major SW128 canonical layout of the MMA (atoms of 8 candidates x 64
-// channels; LBO = 4 KB between channel blocks, SBO = 1 KB between candidate
-// groups).  Padding candidates point past the last row and arrive as zeros.
+// the same B; the fast form keeps only w_hi (8 significant bits).  B is the
+// MN-major SW128 canonical layout (atoms of 8 candidates x 64 channels, the
+// 16-byte pieces of a 128-byte row permuted by the row index; LBO = 4 KB
+// between channel blocks, SBO = 1 KB between candidate groups), filled from
+// the caller's [N][C] rows by the Tensor Memory Accelerator: one
+// cp.async.bulk.tensor tile::gather4 moves four arbitrary sample rows x 64
+// channels with 128-byte swizzling, straight into that layout; padding
+// candidates point past the last row and arrive as zeros.  A warp issues its
+// lanes' gathers one after another (~40 ns each), so the copy rate grows
+// with the number of issuing warps (measured: ~1.9 TB/s over the chip with
+// one warp per SM, ~13 TB/s from L2 with eight); hence eight producer warps.
 //
 // Warp roles (persistent CTA, static round-robin over (tile, slab) items):
 //   warps 0-15 weights: warp w handles target rows 32 (w % 4) .. + 31 (one
 //              TMEM lane quarter, a compact 32-target k-d leaf) and candidates
 //              8 (w / 4) .. + 7 of every chunk; a group of 8 candidates that
 //              cannot reach the quarter (disc of radius quarter radius + r) is
-//              skipped; weight-map sums from the weights the MMA consumes;
-//              epilogue (the quarter's columns split four ways);
-//   warps 16-19 producers (every fourth chunk each): walk the tile's sample
-//              ranges, write tile-relative candidate vectors, issue the TMA
-//              gathers of the chunk's data rows;
-//   warp 20    MMA issue (one lane) and tcgen05.commit.
+//              skipped; weight-map sums; epilogue (the quarter's columns split
+//              four ways);
+//   warps 16-23 producers (chunk q belongs to warp q % 8, which owns stage
+//              q % 8): locate the chunk's candidates in the tile's sample
+//              ranges, write their tile-relative vectors, gather their data
+//              rows; the next own chunk's loads are issued before waiting for
+//              the stage to be free;
+//   warp 24    MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cmath>
 
 #include "cg_common.cuh"
 #include "cg_internal.h"
@@ -47,7 +55,7 @@ namespace {
 constexpr int kT = kTile2;          // targets per tile = MMA M
 constexpr int kK = 32;              // candidates per chunk
 constexpr int kWW = 16;             // weight warps (4 per TMEM lane quarter)
-constexpr int kNP = 4;              // producer warps (chunk q goes to warp q % kNP)
+constexpr int kNP = 8;              // producer warps (chunk q goes to warp q % kNP)
 constexpr int kThreads = (kWW + kNP + 1) * 32;
 constexpr int kProdWarp = kWW;      // first producer warp
 constexpr int kMmaWarp = kWW + kNP;
@@ -62,6 +70,7 @@ struct TcArgs {
   const float4* subf;   // per tile x quarter: centre rel. to the tile centre, chord radius
   const int64_t* range_off;
   const int2* range_s;
+  const int32_t* range_c;
   const int32_t* tile_cand;
   int64_t n_tiles;
   const float4* f1;
@@ -81,6 +90,7 @@ struct TcArgs {
   int split;     // 1: weights as hi + lo BF16 pairs (two MMAs per K step)
   uint32_t tmem_cols;
   KernelDev kd;
+  float q3;      // cubic term of the chord series of d^2 (0 where negligible)
   int mode;      // 0 store, 1 add, 2 one-shot normalised output
   float* acc_num;
   float2* acc_w;
@@ -95,12 +105,14 @@ struct TcArgs {
 
 struct Smem {
   uint8_t* B;          // ns stages of cp * 64 bytes
-  float4* cand;        // ns x kK
-  uint32_t* cidx;      // ns x kK
+  float4* cand;        // ns x kK: tile-relative vector, w = log2(omega)
+  float* reach;        // ns x 4 quarters x kK: squared chord to the quarter centre
+  uint32_t* cidx;      // ns x kK: row of the caller's arrays
   float2* wpart;       // 2 buffers x (kWW / 4) groups x kT partial weight sums
-  uint64_t* full;      // ns
-  uint64_t* afull;     // ns
-  uint64_t* empty;     // ns
+  uint64_t* full;      // ns: data rows landed (TMA transaction bytes)
+  uint64_t* cfull;     // ns: candidate vectors written
+  uint64_t* afull;     // ns: weights in TMEM
+  uint64_t* empty;     // ns: MMAs of the stage done
   uint64_t* dfull;
   uint64_t* dempty;
   uint64_t* fin;
@@ -176,6 +188,94 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo,
   return smem_desc(addr, lbo, sbo) | ((uint64_t)2 << 61);  // layout: 128-byte swizzle
 }
 
+__device__ __forceinline__ int chunks_of(const TcArgs& a, int64_t item) {
+  return (a.tile_cand[item / a.n_slabs] + kK - 1) / kK;
+}
+
+// What a producer lane needs to stage one chunk; loaded one own chunk ahead.
+struct Fetch {
+  int64_t tile;
+  int c_base;
+  int pos;            // sorted sample position of this lane's candidate (-1: padding)
+  float4 h, l;        // its double-float unit vector (h.w = omega)
+  uint32_t idx;       // its row in the caller's arrays
+  float4 chi, clo;    // tile centre (double-float)
+  float4 sq[4];       // quarter centres relative to the tile centre
+};
+
+// Candidates 32 ch .. 32 ch + 31 of the tile of `item`: the first range whose
+// cumulative count covers 32 ch, then a walk through the following ranges
+// held in lanes.
+__device__ __forceinline__ void fetch_chunk(const TcArgs& a, int64_t item, int ch, int lane,
+                                            Fetch& f) {
+  const int64_t tile = item / a.n_slabs;
+  f.tile = tile;
+  f.c_base = (int)(item % a.n_slabs) * a.cp;
+  const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
+  const int c0 = ch * kK;
+  // number of ranges with cum <= c0 (cum is non-decreasing within the tile)
+  int64_t cnt = 0;
+  for (int64_t b = r0; b < r1; b += 32) {
+    const int64_t r = b + lane;
+    const bool le = (r < r1) && a.range_c[r] <= c0;
+    const unsigned m = __ballot_sync(0xffffffffu, le);
+    cnt += __popc(m);
+    if (m != 0xffffffffu) break;
+  }
+  int64_t wbase = r0 + cnt - 1;   // range holding candidate c0
+  int2 wr_lane = make_int2(0, 0);
+  int32_t c_first = 0;
+  if (wbase + lane < r1) wr_lane = a.range_s[wbase + lane];
+  if (lane == 0 && wbase < r1) c_first = a.range_c[wbase];
+  int off = c0 - __shfl_sync(0xffffffffu, c_first, 0);
+  int wr = 0, filled = 0, pos = -1;
+  while (filled < kK) {
+    if (wr == 32) {
+      wbase += 32;
+      wr = 0;
+      if (wbase >= r1) break;
+      wr_lane = (wbase + lane < r1) ? a.range_s[wbase + lane] : make_int2(0, 0);
+    }
+    if (wbase + wr >= r1) break;
+    const int rs = __shfl_sync(0xffffffffu, wr_lane.x, wr);
+    const int re = __shfl_sync(0xffffffffu, wr_lane.y, wr);
+    const int avail = re - rs - off;
+    const int take = min(kK - filled, avail);
+    if (take > 0) {
+      if (lane >= filled && lane < filled + take) pos = rs + off + (lane - filled);
+      filled += take;
+      off += take;
+    }
+    if (off >= re - rs) {
+      ++wr;
+      off = 0;
+    }
+  }
+  f.pos = pos;
+  f.idx = 0xffffffffu;
+  if (pos >= 0) {
+    f.h = a.s_hi[pos];
+    f.l = a.s_lo[pos];
+    f.idx = a.sperm[pos];
+  }
+  f.chi = a.chi[tile];
+  f.clo = a.clo[tile];
+#pragma unroll
+  for (int qq = 0; qq < 4; ++qq) f.sq[qq] = a.subf[tile * 4 + qq];
+}
+
+// Next own chunk: global chunk q + kNP, i.e. kNP chunks further along the
+// CTA's sequence of (item, chunk) pairs.
+__device__ __forceinline__ void advance(const TcArgs& a, int64_t n_items, int64_t& item, int& ch,
+                                        int& nch, int step) {
+  ch += step;
+  while (item < n_items && ch >= nch) {
+    ch -= nch;
+    item += gridDim.x;
+    nch = (item < n_items) ? chunks_of(a, item) : 0;
+  }
+}
+
 template <int KT, bool SPLIT, bool BIG>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ CUtensorMap tmap,
                                                          TcArgs a) {
@@ -189,12 +289,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     p += (size_t)ns * cp * 64;
     S.cand = reinterpret_cast<float4*>(p);
     p += (size_t)ns * kK * sizeof(float4);
+    S.reach = reinterpret_cast<float*>(p);
+    p += (size_t)ns * 4 * kK * sizeof(float);
     S.cidx = reinterpret_cast<uint32_t*>(p);
     p += (size_t)ns * kK * sizeof(uint32_t);
     S.wpart = reinterpret_cast<float2*>(p);
-    p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);  // (unchanged formula, kWW = 16)
+    p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);
     S.full = reinterpret_cast<uint64_t*>(p);
-    S.afull = S.full + kMaxStages;
+    S.cfull = S.full + kMaxStages;
+    S.afull = S.cfull + kMaxStages;
     S.empty = S.afull + kMaxStages;
     S.dfull = S.empty + kMaxStages;
     S.dempty = S.dfull + 1;
@@ -213,9 +316,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   }
   if (tid == 32) {
     for (int s = 0; s < ns; ++s) {
-      mbar_init(&S.full[s], 32);        // producer lanes (+ TMA transaction bytes)
+      mbar_init(&S.full[s], 1);          // producer lane 0 (+ TMA transaction bytes)
+      mbar_init(&S.cfull[s], 32);        // producer lanes, after their vector stores
       mbar_init(&S.afull[s], kWW * 32);  // every weight thread
-      mbar_init(&S.empty[s], 1);        // MMA commit
+      mbar_init(&S.empty[s], 1);         // MMA commit
     }
     mbar_init(S.dfull, 1);
     mbar_init(S.dempty, kWW * 32);
@@ -237,99 +341,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (warp >= kProdWarp && warp < kProdWarp + kNP) {
     // ------------------------------------------------------------ producers
     const int pw = warp - kProdWarp;
-    uint32_t q = 0;
-    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-      const int64_t tile = item / a.n_slabs;
-      const int c_base = (int)(item % a.n_slabs) * cp;
-      const float4 chi = a.chi[tile], clo = a.clo[tile];
-      const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
-      const int total = a.tile_cand[tile];
-      const int nch = (total + kK - 1) / kK;
-      // window of 32 ranges held in lanes
-      int64_t wnext = r0;
-      int wr = 32, off = 0;
-      int2 wrange = make_int2(0, 0);
-      for (int ch = 0; ch < nch; ++ch, ++q) {
-        const int st = (int)(q % (uint32_t)ns);
-        const bool mine = (ch % kNP) == pw;   // every producer walks all chunks
-        if (mine && q >= (uint32_t)ns) {
-          if (!mbar_wait(&S.empty[st], ((q / ns) - 1) & 1, abort_flag)) {
-            set_error(a.err, ERR_TIMEOUT);
-            *abort_flag = 1;
-            break;
-          }
-        }
-        // gather the sorted positions of this chunk's candidates
-        // (every pass either fills candidates or moves to the next range)
-        int mypos = -1;
-        int filled = 0;
-        while (filled < kK) {
-          if (wr == 32) {
-            const int64_t r = wnext + lane;
-            wrange = (r < r1) ? a.range_s[r] : make_int2(0, 0);
-            wnext += 32;
-            wr = 0;
-            off = 0;
-            if (wnext - 32 >= r1) break;
-          }
-          const int rs = __shfl_sync(0xffffffffu, wrange.x, wr);
-          const int re = __shfl_sync(0xffffffffu, wrange.y, wr);
-          const int avail = re - rs - off;
-          const int take = min(kK - filled, avail);
-          if (take > 0 && lane >= filled && lane < filled + take) mypos = rs + off + (lane - filled);
-          filled += max(take, 0);
-          off += max(take, 0);
-          if (off >= re - rs) {
-            ++wr;
-            off = 0;
-          }
-        }
-        if (!mine) continue;
-        // padding candidate: far from every target and from the empty-slot
-        // sentinel (4, 4, 4) of the tile-relative target vectors
-        float4 cb = make_float4(-4.f, -4.f, -4.f, 0.f);
-        uint32_t idx = 0xffffffffu;
-        if (mypos >= 0) {
-          const float4 h = a.s_hi[mypos];
-          const float4 l = a.s_lo[mypos];
-          idx = a.sperm[mypos];
-          cb = make_float4(df_diff(h.x, l.x, chi.x, clo.x), df_diff(h.y, l.y, chi.y, clo.y),
-                           df_diff(h.z, l.z, chi.z, clo.z), h.w);
-        }
-        S.cand[st * kK + lane] = cb;
-        S.cidx[st * kK + lane] = idx;
-        __syncwarp();
-        // data rows -> B stage: TMA gather4 of 4 rows x 64 channels per lane
+    const int nblk = cp / 64;                     // 64-channel blocks of a slab
+    const uint32_t bytes = (uint32_t)kK * (uint32_t)cp * 2u;
+    int64_t item = blockIdx.x;
+    int ch = 0;
+    int nch = (item < n_items) ? chunks_of(a, item) : 0;
+    advance(a, n_items, item, ch, nch, pw);
+    uint32_t q = (uint32_t)pw;
+    Fetch f;
+    if (item < n_items) fetch_chunk(a, item, ch, lane, f);
+    while (item < n_items && !*abort_flag) {
+      const int st = (int)(q % (uint32_t)ns);
+      if (q >= (uint32_t)ns &&
+          !mbar_wait(&S.empty[st], ((q / ns) - 1) & 1, abort_flag)) {
+        set_error(a.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      // candidate vectors: padding lies far from every target and from the
+      // empty-slot sentinel (4, 4, 4) of the tile-relative target vectors
+      float4 cb = make_float4(-4.f, -4.f, -4.f, -INFINITY);
+      if (f.pos >= 0) {
+        const float w = f.h.w;
+        cb = make_float4(df_diff(f.h.x, f.l.x, f.chi.x, f.clo.x),
+                         df_diff(f.h.y, f.l.y, f.chi.y, f.clo.y),
+                         df_diff(f.h.z, f.l.z, f.chi.z, f.clo.z),
+                         (w > 0.f) ? log2f(w) : -INFINITY);
+      }
+      S.cand[st * kK + lane] = cb;
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const float ex = cb.x - f.sq[qq].x, ey = cb.y - f.sq[qq].y, ez = cb.z - f.sq[qq].z;
+        S.reach[(st * 4 + qq) * kK + lane] = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      }
+      S.cidx[st * kK + lane] = f.idx;
+      mbar_arrive(&S.cfull[st]);
+      // data rows -> B stage: lane (j, h) gathers rows 4h .. 4h + 3 of
+      // channel block j (SW128: 8-row atoms 1 KB apart, 4-row halves 512 B)
+      {
         const uint32_t bbase = su32(S.B + (size_t)st * cp * 64);
-        const int nblk = cp / 64;                 // 64-channel blocks
-        const uint32_t bytes = (uint32_t)kK * (uint32_t)cp * 2u;
-        const int row_pad = a.n_rows;             // past the end: zero rows
         int rowk[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const uint32_t rid = __shfl_sync(0xffffffffu, idx, (lane & 7) * 4 + t);
-          rowk[t] = (rid == 0xffffffffu) ? row_pad : (int)rid;
+          const uint32_t rid = __shfl_sync(0xffffffffu, f.idx, (lane & 7) * 4 + t);
+          rowk[t] = (rid == 0xffffffffu) ? a.n_rows : (int)rid;   // past the end: zeros
         }
         if (lane == 0)
-          asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
-                           su32(&S.full[st])),
-                       "r"(bytes)
-                       : "memory");
+          asm volatile(
+              "{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                  su32(&S.full[st])),
+              "r"(bytes)
+              : "memory");
         __syncwarp();
         if (lane < nblk * 8) {
-          const int j = lane >> 3, h = lane & 7;  // channel block, row quad
+          const int j = lane >> 3, h = lane & 7;
           const uint32_t dst = bbase + (uint32_t)j * 4096u + (uint32_t)(h >> 1) * 1024u +
                                (uint32_t)(h & 1) * 512u;
-          const int x = c_base + 64 * j;
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
               " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(rowk[0]), "r"(rowk[1]),
-              "r"(rowk[2]), "r"(rowk[3]), "r"(su32(&S.full[st]))
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(f.c_base + 64 * j), "r"(rowk[0]),
+              "r"(rowk[1]), "r"(rowk[2]), "r"(rowk[3]), "r"(su32(&S.full[st]))
               : "memory");
         }
-        if (lane != 0) mbar_arrive(&S.full[st]);
       }
+      // next own chunk: issue its loads now, consume them after the next wait
+      advance(a, n_items, item, ch, nch, kNP);
+      q += kNP;
+      if (item < n_items) fetch_chunk(a, item, ch, lane, f);
     }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
@@ -338,8 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
                              ((uint32_t)(cp >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
       for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
-        const int64_t tile = item / a.n_slabs;
-        const int nch = (a.tile_cand[tile] + kK - 1) / kK;
+        const int nch = chunks_of(a, item);
         if (tq > 0 && !mbar_wait(S.dempty, (tq - 1) & 1, abort_flag)) {
           set_error(a.err, ERR_TIMEOUT);
           *abort_flag = 1;
@@ -402,9 +480,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int part_cols = cp / 4;             // epilogue columns of this group
     const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
-    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f), q3 = a.kd.k1 * (1.f / 90.f);
+    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f), q3 = a.q3;
     const float q4 = a.kd.k2;
     const float c2_in = a.kd.c2_in, c2_out = a.kd.c2_out;
+    // a pair is inside the guard band iff |c2 - mid| <= half (with slack)
+    const float c2_mid = 0.5f * (c2_in + c2_out);
+    const float c2_half = 0.5f * (c2_out - c2_in) * 1.001f + 1e-30f;
     uint32_t q = 0, tq = 0;
     unsigned npair = 0;
     for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
@@ -420,30 +501,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         f2 = a.f2[slot];
       }
       const uint32_t user = a.perm_t[slot];
-      const int nch = (a.tile_cand[tile] + kK - 1) / kK;
+      const int nch = chunks_of(a, item);
       // the quarter's reach: candidates beyond (quarter radius + r) give w = 0
       const float4 sq = a.subf[tile * 4 + quarter];
       const float reach2 = (rc + sq.w) * (rc + sq.w) * 1.0001f + 1e-12f;
       float ws = 0.f, wc = 0.f;
+      unsigned np_item = 0;
       bool ok = true;
       for (int ch = 0; ch < nch; ++ch, ++q) {
         const int st = (int)(q % (uint32_t)ns);
-        if (!mbar_wait(&S.full[st], (q / ns) & 1, abort_flag)) {
+        if (!mbar_wait(&S.cfull[st], (q / ns) & 1, abort_flag)) {
           ok = false;
           break;
         }
         // ---- 8 weights of this thread's row, branch-free ----
         const int kb = st * kK + grp * 8;
         bool reach = false;
-        if (lane < 8) {
-          const float4 cb = S.cand[kb + lane];
-          const float ex = cb.x - sq.x, ey = cb.y - sq.y, ez = cb.z - sq.z;
-          reach = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= reach2;
-        }
+        if (lane < 8) reach = S.reach[(st * 4 + quarter) * kK + grp * 8 + lane] <= reach2;
         const bool grp_live = __any_sync(0xffffffffu, reach);
         float w[8];
-        uint32_t band = 0;     // pairs whose cut needs the FP64 decision
         if (grp_live) {
+          float c2k[8];
+          float bm = INFINITY;     // distance of the nearest c2 to the band centre
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const float4 cb = S.cand[kb + k];
@@ -454,41 +533,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
               const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
               const float d2 = d * d;
               if (KT == CG_GAUSS1D) {
-                e = q1 * d2;
+                e = fmaf(q1, d2, cb.w);
               } else {
                 const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
                 const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
                 const float s2 = fmaf(ap, ap, bp * bp);
                 const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
-                e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+                e = fmaf(fmaf(q1 * ap, ap, q4 * bp * bp), ratio, cb.w);
               }
             } else if (KT == CG_GAUSS1D) {
-              // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent
-              e = c2 * fmaf(c2, fmaf(c2, q3, q2), q1);
+              // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent,
+              // plus log2(omega)
+              e = fmaf(c2, fmaf(c2, fmaf(c2, q3, q2), q1), cb.w);
             } else {
               // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
               const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
               const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
               const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
-              e = fmaf(q1 * ap, ap, q4 * bp * bp) * ratio;
+              e = fmaf(fmaf(q1 * ap, ap, q4 * bp * bp), ratio, cb.w);
             }
-            const float wk = ex2_approx(e) * cb.w;
+            const float wk = ex2_approx(e);
             const bool in = c2 <= c2_out;
             w[k] = in ? wk : 0.f;
-            npair += (in && slab == 0) ? 1u : 0u;
-            band |= (in && c2 >= c2_in) ? (1u << k) : 0u;
+            np_item += in ? 1u : 0u;
+            bm = fminf(bm, fabsf(c2 - c2_mid));
+            c2k[k] = c2;
           }
           // rare: decide pairs inside the guard band from the FP64 coordinates
-          if (__any_sync(0xffffffffu, band != 0u)) {
+          if (__any_sync(0xffffffffu, bm <= c2_half)) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-              if (band & (1u << k)) {
+              if (c2k[k] >= c2_in && c2k[k] <= c2_out) {
                 const uint32_t idx = S.cidx[kb + k];
                 const double2 tl = a.tll[slot];
                 const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
                 if (!(d <= a.kd.r_rad)) {
                   w[k] = 0.f;
-                  if (slab == 0) --npair;
+                  --np_item;
                 }
               }
             }
@@ -544,7 +625,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         fence_before();
         mbar_arrive(&S.afull[st]);
       }
-      // ---- epilogue: combine the two weight-map partials of this row ----
+      if (slab == 0) npair += np_item;
+      // ---- epilogue: combine the weight-map partials of this row ----
       constexpr int kGroups = kWW / 4;
       float2* wp = S.wpart + (size_t)(tq & 1) * kGroups * kT;   // double buffered
       wp[grp * kT + row] = make_float2(ws, wc);
@@ -647,8 +729,8 @@ KernFn pick_kernel(int kt, bool split, bool big) {
 }
 
 size_t smem_bytes(int cp, int ns) {
-  return (size_t)ns * cp * 64 + (size_t)ns * kK * (sizeof(float4) + sizeof(uint32_t)) +
-         (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (3 * kMaxStages + 4) * sizeof(uint64_t) +
+  return (size_t)ns * cp * 64 + (size_t)ns * kK * (sizeof(float4) + 4 * sizeof(float) + sizeof(uint32_t)) +
+         (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (4 * kMaxStages + 4) * sizeof(uint64_t) +
          16;
 }
 
@@ -682,6 +764,7 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.subf = t.subf;
   a.range_off = t.range_off;
   a.range_s = t.range_s;
+  a.range_c = t.range_c;
   a.tile_cand = t.tile_cand;
   a.n_tiles = t.n_tiles;
   a.f1 = g->tgt_f1;
@@ -699,6 +782,12 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.cp = (slab + 63) / 64 * 64;
   a.n_slabs = (g->C + a.cp - 1) / a.cp;
   a.kd = g->kdev;
+  // the c^4/90 term of d^2 changes the exponent by |k1| c2^3 / 90; dropped
+  // where that stays below 1e-9 at the support radius
+  a.q3 = (std::fabs(g->kdev.k1) * (double)g->kdev.c2_out * g->kdev.c2_out * g->kdev.c2_out / 90.0 >
+          1e-9)
+             ? g->kdev.k1 * (1.f / 90.f)
+             : 0.f;
   a.mode = mode;
   a.acc_num = g->acc_num;
   a.acc_w = g->acc_w;
@@ -712,12 +801,14 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   // Stages: chunk q uses stage q % ns and is staged by producer warp q % kNP.
   // ns must be a multiple of kNP so that every stage always belongs to the
   // same producer warp: the parity-based empty-barrier wait is only valid
-  // while its waiter is at most one phase ahead, which a second producer
-  // racing through the same stage could break.  8 stages of split weights
-  // (32 TMEM columns each) plus a 256-column accumulator fill 512 columns.
+  // while its waiter is at most one phase ahead, and two producers sharing a
+  // stage would also interleave their transaction counts on its barrier.
+  // 8 stages of split weights (32 TMEM columns each) plus a 256-column
+  // accumulator fill 512 columns.
   a.split = split ? 1 : 0;
   const int ns = 8;
   static_assert(8 % kNP == 0, "stages must be a multiple of the producer warps");
+  static_assert(kMaxStages >= 8, "stage barriers");
   const uint32_t acols = split ? 32u : 16u;
   uint32_t need = (uint32_t)a.cp + acols * ns;
   uint32_t cols = 32;

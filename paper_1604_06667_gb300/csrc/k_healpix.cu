@@ -296,21 +296,46 @@ __device__ __forceinline__ int32_t lower_bound_u32(const uint32_t* __restrict__ 
   return lo;
 }
 
-__global__ void k_sample_ranges(const Range* __restrict__ ranges, int64_t n_ranges,
-                                const int32_t* __restrict__ ring_off,
-                                const uint32_t* __restrict__ skey, int2* __restrict__ out,
-                                int32_t* __restrict__ tile_cand) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_ranges) return;
-  const Range q = ranges[r];
-  const int32_t a = ring_off[q.ring], b = ring_off[q.ring + 1];
-  int32_t lo = a, hi = a;
-  if (b > a) {
-    lo = lower_bound_u32(skey, a, b, (uint32_t)q.pix_lo);
-    hi = lower_bound_u32(skey, lo, b, (uint32_t)q.pix_hi + 1u);
+// One warp per tile: the sorted-sample interval [lo, hi) of each of the
+// tile's pixel ranges (binary search inside the range's ring), the number of
+// the tile's candidates before each range (cum), and the tile's total.
+__global__ void k_tile_ranges(const Range* __restrict__ ranges,
+                              const int64_t* __restrict__ range_off, int64_t n_tiles,
+                              const int32_t* __restrict__ ring_off,
+                              const uint32_t* __restrict__ skey, int2* __restrict__ out,
+                              int32_t* __restrict__ cum, int32_t* __restrict__ tile_cand) {
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= n_tiles) return;
+  const int64_t r0 = range_off[tile], r1 = range_off[tile + 1];
+  int32_t running = 0;
+  for (int64_t b = r0; b < r1; b += 32) {
+    const int64_t r = b + lane;
+    int32_t lo = 0, hi = 0;
+    if (r < r1) {
+      const Range q = ranges[r];
+      const int32_t a = ring_off[q.ring], e = ring_off[q.ring + 1];
+      lo = a;
+      hi = a;
+      if (e > a) {
+        lo = lower_bound_u32(skey, a, e, (uint32_t)q.pix_lo);
+        hi = lower_bound_u32(skey, lo, e, (uint32_t)q.pix_hi + 1u);
+      }
+    }
+    const int32_t cnt = hi - lo;
+    int32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (r < r1) {
+      out[r] = make_int2(lo, hi);
+      cum[r] = running + incl - cnt;
+    }
+    running += __shfl_sync(0xffffffffu, incl, 31);
   }
-  out[r] = make_int2(lo, hi);
-  if (hi > lo) atomicAdd(&tile_cand[q.pad], hi - lo);
+  if (lane == 0) tile_cand[tile] = running;
 }
 
 __global__ void k_export(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
@@ -353,6 +378,7 @@ void tiling_free(Tiling& t, cudaStream_t s) {
   dfree(t.range_off, s);
   dfree(t.ranges, s);
   dfree(t.range_s, s);
+  dfree(t.range_c, s);
   t.n_ranges = 0;
 }
 
@@ -365,6 +391,7 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   dfree(t.range_off, s);
   dfree(t.ranges, s);
   dfree(t.range_s, s);
+  dfree(t.range_c, s);
   if ((e = dalloc(&counts, (size_t)nt, s)) != cudaSuccess) return e;
   const int warps = 8;
   k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, t.sub64, nt, g->nside, r,
@@ -382,6 +409,7 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   if ((e = dalloc(&t.range_off, (size_t)nt + 1, s)) != cudaSuccess) { free(h); return e; }
   if ((e = dalloc(&t.ranges, (size_t)t.n_ranges, s)) != cudaSuccess) { free(h); return e; }
   if ((e = dalloc(&t.range_s, (size_t)t.n_ranges, s)) != cudaSuccess) { free(h); return e; }
+  if ((e = dalloc(&t.range_c, (size_t)t.n_ranges, s)) != cudaSuccess) { free(h); return e; }
   e = cudaMemcpyAsync(t.range_off, h, sizeof(int64_t) * (size_t)(nt + 1),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -437,12 +465,11 @@ cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
                                                    weights, n, g->s_hi, g->s_lo, g->d_err);
   k_ring_off<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, g->sorted_key, n, g->ring_off);
   g->n_launches += 2;
-  cudaError_t e = cudaMemsetAsync(t.tile_cand, 0, sizeof(int32_t) * (size_t)t.n_tiles, s);
-  if (e != cudaSuccess) return e;
-  if (t.n_ranges > 0) {
-    k_sample_ranges<<<ceil_div(t.n_ranges, 256), 256, 0, s>>>(t.ranges, t.n_ranges, g->ring_off,
-                                                              g->sorted_key, t.range_s,
-                                                              t.tile_cand);
+  if (t.n_tiles > 0) {
+    const int warps = 8;
+    k_tile_ranges<<<ceil_div(t.n_tiles, warps), 32 * warps, 0, s>>>(
+        t.ranges, t.range_off, t.n_tiles, g->ring_off, g->sorted_key, t.range_s, t.range_c,
+        t.tile_cand);
     g->n_launches += 1;
   }
   g->last_n = n;

@@ -26,18 +26,18 @@
 // one warp per SM, ~13 TB/s from L2 with eight); hence eight producer warps.
 //
 // Warp roles (persistent CTA, static round-robin over (tile, slab) items):
-//   warps 0-15 weights: warp w handles target rows 32 (w % 4) .. + 31 (one
+//   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 (one
 //              TMEM lane quarter, a compact 32-target k-d leaf) and candidates
-//              8 (w / 4) .. + 7 of every chunk; a group of 8 candidates that
-//              cannot reach the quarter (disc of radius quarter radius + r) is
-//              skipped; weight-map sums; epilogue (the quarter's columns split
-//              four ways);
-//   warps 16-23 producers (chunk q belongs to warp q % 8, which owns stage
+//              16 (w / 4) .. + 15 of every chunk, as two groups of 8; a group
+//              that cannot reach the quarter (disc of radius quarter radius +
+//              r) is skipped; weight-map sums; epilogue (the quarter's columns
+//              split two ways);
+//   warps 8-15 producers (chunk q belongs to warp q % 8, which owns stage
 //              q % 8): locate the chunk's candidates in the tile's sample
 //              ranges, write their tile-relative vectors, gather their data
 //              rows; the next own chunk's loads are issued before waiting for
 //              the stage to be free;
-//   warp 24    MMA issue (one lane) and tcgen05.commit.
+//   warp 16    MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
 #include <cuda.h>
@@ -54,14 +54,19 @@ namespace {
 
 constexpr int kT = kTile2;          // targets per tile = MMA M
 constexpr int kK = 32;              // candidates per chunk
-constexpr int kWW = 16;             // weight warps (4 per TMEM lane quarter)
+constexpr int kWW = 8;              // weight warps (2 per TMEM lane quarter)
+constexpr int kGPW = 2;             // groups of 8 candidates per weight warp and chunk
+static_assert(kGPW * 8 * (kWW / 4) == 32, "weight warps cover a chunk");
 constexpr int kNP = 8;              // producer warps (chunk q goes to warp q % kNP)
 constexpr int kThreads = (kWW + kNP + 1) * 32;
 constexpr int kProdWarp = kWW;      // first producer warp
 constexpr int kMmaWarp = kWW + kNP;
-constexpr int kMaxStages = 8;
+constexpr int kNS = 8;             // pipeline stages (one per producer warp)
+constexpr int kMaxStages = kNS;
 // a wait gives up after ~1 s of SM clock (or at once after another role gave up)
 constexpr long long kWaitCycles = 2000000000LL;
+// longest single suspension inside a wait (ns); the time-out is checked between
+constexpr uint32_t kSuspendNs = 20000;
 
 struct TcArgs {
   const float4* chi;
@@ -86,11 +91,9 @@ struct TcArgs {
   int C;
   int cp;        // padded channels per slab (multiple of 64, <= 256)
   int n_slabs;
-  int ns;        // pipeline stages
   int split;     // 1: weights as hi + lo BF16 pairs (two MMAs per K step)
   uint32_t tmem_cols;
   KernelDev kd;
-  float q3;      // cubic term of the chord series of d^2 (0 where negligible)
   int mode;      // 0 store, 1 add, 2 one-shot normalised output
   float* acc_num;
   float2* acc_w;
@@ -142,14 +145,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity,
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
+    // the suspend-time hint lets the warp sleep until the phase completes
+    // (or the hint expires) instead of re-issuing the test
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
-    if ((it & 63u) == 63u) {
+    if ((it & 3u) == 3u) {
       if (*abort_flag) return false;
       if (clock64() - t0 > kWaitCycles) return false;
     }
@@ -280,7 +285,7 @@ template <int KT, bool SPLIT, bool BIG>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ CUtensorMap tmap,
                                                          TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const int ns = a.ns;
+  constexpr int ns = kNS;
   const int cp = a.cp;
   Smem S;
   {
@@ -351,9 +356,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     Fetch f;
     if (item < n_items) fetch_chunk(a, item, ch, lane, f);
     while (item < n_items && !*abort_flag) {
-      const int st = (int)(q % (uint32_t)ns);
-      if (q >= (uint32_t)ns &&
-          !mbar_wait(&S.empty[st], ((q / ns) - 1) & 1, abort_flag)) {
+      const int st = (int)(q % (uint32_t)kNS);
+      if (q >= (uint32_t)kNS &&
+          !mbar_wait(&S.empty[st], ((q / kNS) - 1) & 1, abort_flag)) {
         set_error(a.err, ERR_TIMEOUT);
         *abort_flag = 1;
         break;
@@ -426,8 +431,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         fence_after();
         bool ok = true;
         for (int ch = 0; ch < nch; ++ch, ++q) {
-          const int st = (int)(q % (uint32_t)ns);
-          const uint32_t ph = (q / ns) & 1;
+          const int st = (int)(q % (uint32_t)kNS);
+          const uint32_t ph = (q / kNS) & 1;
           if (!mbar_wait(&S.full[st], ph, abort_flag) ||
               !mbar_wait(&S.afull[st], ph, abort_flag)) {
             ok = false;
@@ -476,11 +481,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     // ------------------------------------------------------------ weights
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;      // TMEM lane = target row
-    const int grp = warp >> 2;                // candidates 8 grp .. 8 grp + 7
+    const int grp = warp >> 2;                // candidates 16 grp .. 16 grp + 15
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const int part_cols = cp / 4;             // epilogue columns of this group
+    const int part_cols = cp / (kWW / 4);     // epilogue columns of this warp
     const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
-    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f), q3 = a.q3;
+    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f);
     const float q4 = a.kd.k2;
     const float c2_in = a.kd.c2_in, c2_out = a.kd.c2_out;
     // a pair is inside the guard band iff |c2 - mid| <= half (with slack)
@@ -509,19 +514,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       unsigned np_item = 0;
       bool ok = true;
       for (int ch = 0; ch < nch; ++ch, ++q) {
-        const int st = (int)(q % (uint32_t)ns);
-        if (!mbar_wait(&S.cfull[st], (q / ns) & 1, abort_flag)) {
+        const int st = (int)(q % (uint32_t)kNS);
+        if (!mbar_wait(&S.cfull[st], (q / kNS) & 1, abort_flag)) {
           ok = false;
           break;
         }
-        // ---- 8 weights of this thread's row, branch-free ----
-        const int kb = st * kK + grp * 8;
-        bool reach = false;
-        if (lane < 8) reach = S.reach[(st * 4 + quarter) * kK + grp * 8 + lane] <= reach2;
-        const bool grp_live = __any_sync(0xffffffffu, reach);
-        float w[8];
-        if (grp_live) {
-          float c2k[8];
+        // ---- 2 x 8 weights of this thread's row, branch-free ----
+        uint32_t packed[8], packed_lo[8];
+        float part = 0.f;
+#pragma unroll
+        for (int gi = 0; gi < kGPW; ++gi) {
+          const int g = grp * kGPW + gi;
+          const int kb = st * kK + g * 8;
+          bool reach = false;
+          if (lane < 8) reach = S.reach[(st * 4 + quarter) * kK + g * 8 + lane] <= reach2;
+          const bool grp_live = __any_sync(0xffffffffu, reach);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            packed[gi * 4 + j] = 0u;
+            packed_lo[gi * 4 + j] = 0u;
+          }
+          if (!grp_live) continue;
+          float w[8], c2k[8];
           float bm = INFINITY;     // distance of the nearest c2 to the band centre
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -542,9 +556,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
                 e = fmaf(fmaf(q1 * ap, ap, q4 * bp * bp), ratio, cb.w);
               }
             } else if (KT == CG_GAUSS1D) {
-              // d^2 = c^2 (1 + c^2/12 + c^4/90), folded into the exponent,
-              // plus log2(omega)
-              e = fmaf(c2, fmaf(c2, fmaf(c2, q3, q2), q1), cb.w);
+              // d^2 = c^2 (1 + c^2/12) (the c^4/90 term is below FP32 here),
+              // folded into the exponent, plus log2(omega)
+              e = fmaf(c2, fmaf(c2, q2, q1), cb.w);
             } else {
               // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
               const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
@@ -574,28 +588,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
               }
             }
           }
-        } else {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) w[k] = 0.f;
-        }
-        uint32_t packed[4], packed_lo[4];
-        float part = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          part += w[2 * j] + w[2 * j + 1];
-          if (SPLIT) {
-            // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
-            // truncation), w_lo = w - w_hi is exact in FP32, then rounded
-            const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
-            const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
-            packed[j] = __byte_perm(u0, u1, 0x7632);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
-                                                            w[2 * j + 1] - __uint_as_float(u1));
-            packed_lo[j] = *reinterpret_cast<const uint32_t*>(&l2);
-          } else {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
-            packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
-            packed_lo[j] = 0u;
+          for (int j = 0; j < 4; ++j) {
+            part += w[2 * j] + w[2 * j + 1];
+            if (SPLIT) {
+              // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
+              // truncation), w_lo = w - w_hi is exact in FP32, then rounded
+              const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
+              const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
+              packed[gi * 4 + j] = __byte_perm(u0, u1, 0x7632);
+              const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
+                                                              w[2 * j + 1] - __uint_as_float(u1));
+              packed_lo[gi * 4 + j] = *reinterpret_cast<const uint32_t*>(&l2);
+            } else {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
+              packed[gi * 4 + j] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
           }
         }
         // Kahan accumulation of the chunk partial into the weight map
@@ -606,20 +614,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           ws = t;
         }
         {
-          // candidates 8 grp .. 8 grp + 7 = K step grp / 2, half grp % 2:
-          // split: hi at columns 16 (grp / 2) + 4 (grp % 2), lo 8 further
-          const uint32_t col = SPLIT ? (uint32_t)((grp >> 1) * 16 + (grp & 1) * 4)
-                                     : (uint32_t)((grp >> 1) * 8 + (grp & 1) * 4);
+          // candidates 16 grp .. 16 grp + 15 = K step grp: split: hi at
+          // columns 16 grp .. + 7, lo at 16 grp + 8 .. + 15; single: 8 grp
+          const uint32_t col = SPLIT ? (uint32_t)(grp * 16) : (uint32_t)(grp * 8);
           const uint32_t ta_addr = tmem_a + lane_off + st * acols + col;
-          asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta_addr),
-                       "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3])
-                       : "memory");
+          asm volatile(
+              "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                  ta_addr),
+              "r"(packed[0]), "r"(packed[1]), "r"(packed[2]), "r"(packed[3]), "r"(packed[4]),
+              "r"(packed[5]), "r"(packed[6]), "r"(packed[7])
+              : "memory");
           if (SPLIT)
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(
-                             ta_addr + 8u),
-                         "r"(packed_lo[0]), "r"(packed_lo[1]), "r"(packed_lo[2]),
-                         "r"(packed_lo[3])
-                         : "memory");
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                    ta_addr + 8u),
+                "r"(packed_lo[0]), "r"(packed_lo[1]), "r"(packed_lo[2]), "r"(packed_lo[3]),
+                "r"(packed_lo[4]), "r"(packed_lo[5]), "r"(packed_lo[6]), "r"(packed_lo[7])
+                : "memory");
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
@@ -782,12 +793,6 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.cp = (slab + 63) / 64 * 64;
   a.n_slabs = (g->C + a.cp - 1) / a.cp;
   a.kd = g->kdev;
-  // the c^4/90 term of d^2 changes the exponent by |k1| c2^3 / 90; dropped
-  // where that stays below 1e-9 at the support radius
-  a.q3 = (std::fabs(g->kdev.k1) * (double)g->kdev.c2_out * g->kdev.c2_out * g->kdev.c2_out / 90.0 >
-          1e-9)
-             ? g->kdev.k1 * (1.f / 90.f)
-             : 0.f;
   a.mode = mode;
   a.acc_num = g->acc_num;
   a.acc_w = g->acc_w;
@@ -806,14 +811,12 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   // 8 stages of split weights (32 TMEM columns each) plus a 256-column
   // accumulator fill 512 columns.
   a.split = split ? 1 : 0;
-  const int ns = 8;
-  static_assert(8 % kNP == 0, "stages must be a multiple of the producer warps");
-  static_assert(kMaxStages >= 8, "stage barriers");
+  constexpr int ns = kNS;
+  static_assert(kNS % kNP == 0, "stages must be a multiple of the producer warps");
   const uint32_t acols = split ? 32u : 16u;
   uint32_t need = (uint32_t)a.cp + acols * ns;
   uint32_t cols = 32;
   while (cols < need) cols <<= 1;
-  a.ns = ns;
   a.tmem_cols = cols;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -840,7 +843,12 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  auto kern = pick_kernel(a.kd.type, split != 0, a.kd.big_support != 0);
+  // the series form drops the c^4/90 term of d^2, which changes the exponent
+  // by |k1| c2^3 / 90; where that could exceed 1e-9 at the support radius the
+  // exact 2 asin(c / 2) form is used instead
+  const double c2o = g->kdev.c2_out;
+  const bool big = g->kdev.big_support != 0 || std::fabs(g->kdev.k1) * c2o * c2o * c2o / 90.0 > 1e-9;
+  auto kern = pick_kernel(a.kd.type, split != 0, big);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -194,6 +194,16 @@ cg_status cg_read_timing(cg_grid* g, double* ms, int64_t* n_grid_launches);
 cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* lat_deg,
                           int64_t n, int64_t* pix, void* stream);
 
+/* Unit vectors (cos b cos l, cos b sin l, sin b) of n directions, evaluated
+ * exactly as the gridder evaluates sample positions (the distance of Eq. 1-2
+ * is taken between such vectors): double-float sine and cosine on the FP32
+ * pipes, absolute error ~1e-14, returned as float64.
+ *   lon_deg, lat_deg  device [n] float64 (finite; |lat| <= 90 for a unit vector)
+ *   xyz               device [n][3] float64, written
+ * Asynchronous on `stream`; CG_EINVAL for n < 0 or a null pointer. */
+cg_status cg_unit_vectors(const double* lon_deg, const double* lat_deg, int64_t n, double* xyz,
+                          void* stream);
+
 /* Copy out the sample index built by the last cg_grid_add (the sorted
  * replacement for the paper's hash tables, Sect. 3.4):
  *   sorted_pix  device [n] int64: RING indices in ascending order;

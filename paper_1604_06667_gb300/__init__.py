@@ -4,11 +4,11 @@ The compute path is the CUDA library behind the C ABI in include/cygrid_gb300.h;
 this package is its thin Python binding.  Submodules load lazily so that
 ``import paper_1604_06667_gb300`` works on machines without a GPU.
 """
-__all__ = ["Gridder", "ang2pix_ring", "build"]
+__all__ = ["Gridder", "ang2pix_ring", "unit_vectors", "build"]
 
 
 def __getattr__(name):
-    if name in ("Gridder", "ang2pix_ring"):
+    if name in ("Gridder", "ang2pix_ring", "unit_vectors"):
         from . import gridder
         return getattr(gridder, name)
     if name == "build":

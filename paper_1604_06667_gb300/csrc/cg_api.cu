@@ -108,6 +108,8 @@ void free_all(cg_grid* g) {
   dfree(g->sw.totals, s);
   dfree(g->s_hi, s);
   dfree(g->s_lo, s);
+  dfree(g->u_hi, s);
+  dfree(g->u_lo, s);
   dfree(g->ring_off, s);
   dfree(g->acc_num, s);
   dfree(g->acc_w, s);
@@ -160,7 +162,7 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
   CG_CUDA(cudaSetDevice(g->device), where);
   Tiling& t = tc ? g->t128 : g->t64;
   cudaEvent_t t0 = tmark(g);
-  CG_CUDA(samples_keys(g, lon, lat, n), where);
+  CG_CUDA(samples_keys(g, lon, lat, weights, n), where);
   cudaEvent_t t1 = tmark(g);
   CG_CUDA(samples_sort(g, n), where);
   cudaEvent_t t2 = tmark(g);
@@ -438,6 +440,17 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
     return fail(CG_EINVAL, "cg_ang2pix_ring: null pointer");
   CG_CUDA(ang2pix_export(nside, lon_deg, lat_deg, n, pix, static_cast<cudaStream_t>(stream)),
           "cg_ang2pix_ring");
+  return CG_OK;
+}
+
+cg_status cg_unit_vectors(const double* lon_deg, const double* lat_deg, int64_t n, double* xyz,
+                          void* stream) {
+  g_last_error.clear();
+  if (n < 0) return fail(CG_EINVAL, "cg_unit_vectors: n < 0");
+  if (n > 0 && (!lon_deg || !lat_deg || !xyz))
+    return fail(CG_EINVAL, "cg_unit_vectors: null pointer");
+  CG_CUDA(unit_vectors(lon_deg, lat_deg, n, xyz, static_cast<cudaStream_t>(stream)),
+          "cg_unit_vectors");
   return CG_OK;
 }
 

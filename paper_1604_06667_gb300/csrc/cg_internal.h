@@ -103,6 +103,8 @@ struct cg_grid {
   uint32_t* sorted_val = nullptr;
   float4* s_hi = nullptr;         // [cap_n] sorted samples: unit vector hi, w = omega
   float4* s_lo = nullptr;         // [cap_n] unit vector lo
+  float4* u_hi = nullptr;         // [cap_n] input order: unit vector hi, w = omega
+  float4* u_lo = nullptr;         // [cap_n] input order: unit vector lo
   int32_t* ring_off = nullptr;    // [4*nside + 1]
   int64_t last_n = 0;
   int64_t total_n = 0;
@@ -148,7 +150,10 @@ cudaError_t targets_set_axes(cg_grid* g, double pa_deg);
 // k_healpix.cu -- ang2pix, ring offsets, tile disc queries, sample ranges.
 cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int64_t n,
                            int64_t* pix, cudaStream_t s);
-cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, int64_t n);
+cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const float* weights,
+                         int64_t n);
+cudaError_t unit_vectors(const double* lon, const double* lat, int64_t n, double* out,
+                         cudaStream_t s);
 cudaError_t samples_sort(cg_grid* g, int64_t n);
 cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
                             const float* weights, int64_t n, Tiling& t);

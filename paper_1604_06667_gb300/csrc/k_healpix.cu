@@ -12,6 +12,7 @@
 //             by two binary searches inside its ring.
 #include "cg_common.cuh"
 #include "cg_internal.h"
+#include "cg_trig.cuh"
 
 namespace cg {
 namespace {
@@ -209,81 +210,174 @@ __device__ __forceinline__ bool valid_coord(double lon, double lat) {
   return isfinite(lon) && isfinite(lat) && lat >= -90.0 && lat <= 90.0;
 }
 
+// HEALPix RING index from an approximate z = sin(lat) (|error| ~1e-14):
+// the same decisions as ang2pix_ring_f64, each checked for a margin that the
+// FP64 evaluation's own rounding cannot cross; *ok = false when a value lies
+// within that margin of a decision boundary (then the exact FP64 routine
+// decides).  For nside <= 16384 a truncated quantity is at most 4 nside =
+// 65536 and FP64 and this evaluation differ by < 1e-9 there; the margin is
+// 1e-6.
+__device__ __forceinline__ int64_t ang2pix_ring_fast(int64_t ns, double lon_deg, double z,
+                                                     bool* ok) {
+  constexpr double M = 1e-6;
+  const double za = fabs(z);
+  const double phi = lon_fold_deg(lon_deg);
+  const double tt = phi * (1.0 / 90.0);
+  const double dns = (double)ns;
+  bool good = fabs(za - 2.0 / 3.0) > 1e-9;
+  int64_t pix;
+  if (za <= 2.0 / 3.0) {
+    const double u = dns * (0.5 + tt);
+    const double v = dns * (z * 0.75);
+    const double A = u - v, B = u + v;
+    const double fa = A - floor(A), fb = B - floor(B);
+    good = good && fa > M && fa < 1.0 - M && fb > M && fb < 1.0 - M;
+    const int64_t asc = (int64_t)A;
+    const int64_t dsc = (int64_t)B;
+    const int64_t k = ns + 1 + asc - dsc;
+    const int64_t odd = k & 1;
+    int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
+    j %= 4 * ns;
+    if (j < 0) j += 4 * ns;
+    pix = 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
+  } else {
+    const double ft = tt - floor(tt);
+    // near a pole sqrt(1 - za) magnifies the error of z: leave it to FP64
+    good = good && ft > 1e-12 && ft < 1.0 - 1e-12 && 1.0 - za > 1e-6;
+    const double x = dns * sqrt(3.0 * (1.0 - za));
+    const double P = ft * x, Q = (1.0 - ft) * x;
+    const double fp = P - floor(P), fq = Q - floor(Q);
+    good = good && fp > M && fp < 1.0 - M && fq > M && fq < 1.0 - M;
+    const int64_t a = (int64_t)P;
+    const int64_t b = (int64_t)Q;
+    const int64_t k = a + b + 1;
+    const double J = tt * (double)k;
+    const double fj = J - floor(J);
+    good = good && fj > M && fj < 1.0 - M;
+    int64_t j = (int64_t)J;
+    j %= 4 * k;
+    if (j < 0) j += 4 * k;
+    pix = (z > 0.0) ? 2 * k * (k - 1) + j : 12 * ns * ns - 2 * k * (k + 1) + j;
+  }
+  *ok = good;
+  return pix;
+}
+
+// RING index of a valid sample with z from the double-float sine; exact
+// FP64 fallback near decision boundaries.
+__device__ __forceinline__ int64_t ang2pix_ring_dual(int64_t ns, double lon, double lat,
+                                                     df32 sb) {
+  if (ns > 16384) return ang2pix_ring_f64(ns, lon, lat);
+  bool ok;
+  const int64_t p = ang2pix_ring_fast(ns, lon, (double)sb.hi + (double)sb.lo, &ok);
+  return ok ? p : ang2pix_ring_f64(ns, lon, lat);
+}
+
 __global__ void k_ang2pix_export(int64_t ns, const double* __restrict__ lon,
                                  const double* __restrict__ lat, int64_t n,
                                  int64_t* __restrict__ pix) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double lo = lon[i], la = lat[i];
-  pix[i] = valid_coord(lo, la) ? ang2pix_ring_f64(ns, lo, la) : -1;
+  if (!valid_coord(lo, la)) {
+    pix[i] = -1;
+    return;
+  }
+  df32 sb, cb;
+  df_sincos_deg(la, sb, cb);
+  pix[i] = ang2pix_ring_dual(ns, lo, la, sb);
 }
 
-// Sample keys: RING index (invalid samples get npix and sort to the end).
+// Unit vectors (double-float) of n directions, as FP64 [n][3].
+__global__ void k_unit_vectors(const double* __restrict__ lon, const double* __restrict__ lat,
+                               int64_t n, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  df32 sb, cb, sl, cl;
+  df_sincos_deg(lat[i], sb, cb);
+  df_sincos_deg(lon[i], sl, cl);
+  const df32 x = df_mul(cb, cl), y = df_mul(cb, sl);
+  out[3 * i + 0] = (double)x.hi + (double)x.lo;
+  out[3 * i + 1] = (double)y.hi + (double)y.lo;
+  out[3 * i + 2] = (double)sb.hi + (double)sb.lo;
+}
+
+// Per sample (input order): RING key (invalid samples get npix and sort to
+// the end), identity value for the sort, and the unit vector as (hi, lo)
+// FP32 pairs with w = sample weight.
 __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
-                              const double* __restrict__ lat, int64_t n,
+                              const double* __restrict__ lat,
+                              const float* __restrict__ weights, int64_t n,
                               uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                              float4* __restrict__ u_hi, float4* __restrict__ u_lo,
                               unsigned* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double lo = lon[i], la = lat[i];
-  uint32_t k;
-  if (valid_coord(lo, la)) {
-    k = (uint32_t)ang2pix_ring_f64(ns, lo, la);
-  } else {
-    k = (uint32_t)(12 * ns * ns);
-    set_error(err, ERR_BAD_SAMPLE);
-  }
-  key[i] = k;
   val[i] = (uint32_t)i;
-}
-
-// Sorted samples: unit vector as (hi, lo) float pairs, w = sample weight.
-__global__ void k_sample_gather(int64_t ns, const uint32_t* __restrict__ skey,
-                                const uint32_t* __restrict__ sval,
-                                const double* __restrict__ lon, const double* __restrict__ lat,
-                                const float* __restrict__ weights, int64_t n,
-                                float4* __restrict__ s_hi, float4* __restrict__ s_lo,
-                                unsigned* err) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t idx = sval[s];
-  if ((int64_t)skey[s] >= 12 * ns * ns) {
-    s_hi[s] = make_float4(4.f, 4.f, 4.f, 0.f);
-    s_lo[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!valid_coord(lo, la)) {
+    key[i] = (uint32_t)(12 * ns * ns);
+    u_hi[i] = make_float4(4.f, 4.f, 4.f, 0.f);
+    u_lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    set_error(err, ERR_BAD_SAMPLE);
     return;
   }
-  double sb, cb, sl, cl;
-  sincos(lat[idx] * kDeg2Rad, &sb, &cb);
-  sincos(lon[idx] * kDeg2Rad, &sl, &cl);
-  float hx, lx, hy, ly, hz, lz;
-  split_f64(cb * cl, hx, lx);
-  split_f64(cb * sl, hy, ly);
-  split_f64(sb, hz, lz);
+  df32 sb, cb, sl, cl;
+  df_sincos_deg(la, sb, cb);
+  df_sincos_deg(lo, sl, cl);
+  key[i] = (uint32_t)ang2pix_ring_dual(ns, lo, la, sb);
+  const df32 x = df_mul(cb, cl), y = df_mul(cb, sl);
   float w = 1.f;
   if (weights) {
-    w = weights[idx];
+    w = weights[i];
     if (!(w >= 0.f) || !isfinite(w)) {
       set_error(err, ERR_BAD_SAMPLE);
       w = 0.f;
     }
   }
-  s_hi[s] = make_float4(hx, hy, hz, w);
-  s_lo[s] = make_float4(lx, ly, lz, 0.f);
+  u_hi[i] = make_float4(x.hi, y.hi, sb.hi, w);
+  u_lo[i] = make_float4(x.lo, y.lo, sb.lo, 0.f);
 }
 
-// ring_off[i] = first sorted position with ring >= i, i = 0 .. 4ns.
-__global__ void k_ring_off(int64_t ns, const uint32_t* __restrict__ skey, int64_t n,
-                           int32_t* __restrict__ ring_off) {
+// Ring number of pixel p (RING scheme); the belt division by 4 ns is a
+// shift when nside is a power of two (log2 given, else -1).
+__device__ __forceinline__ int64_t ring_of_key(int64_t ns, int lg, int64_t p) {
+  const int64_t ncap = 2 * ns * (ns - 1);
+  if (p >= ncap && p < 12 * ns * ns - ncap)
+    return ns + (lg >= 0 ? ((p - ncap) >> (lg + 2)) : (p - ncap) / (4 * ns));
+  return ring_of_pix(ns, p);
+}
+
+// Sorted order: gather the unit vectors, and ring_off[i] = first sorted
+// position with ring >= i, i = 0 .. 4 ns (thread s writes the entries for
+// the rings after its predecessor's ring up to its own).
+__global__ void k_sample_gather(int64_t ns, int lg, const uint32_t* __restrict__ skey,
+                                const uint32_t* __restrict__ sval,
+                                const float4* __restrict__ u_hi,
+                                const float4* __restrict__ u_lo, int64_t n,
+                                float4* __restrict__ s_hi, float4* __restrict__ s_lo,
+                                int32_t* __restrict__ ring_off) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s > n) return;
+  const int lane = threadIdx.x & 31;
   const int64_t npix = 12 * ns * ns;
   const int64_t end = 4 * ns;
-  auto ring = [&](int64_t q) -> int64_t {
-    const int64_t k = skey[q];
-    return (k >= npix) ? end : (int64_t)ring_of_pix(ns, k);
-  };
-  const int64_t rc = (s < n) ? ring(s) : end;
-  const int64_t rp = (s == 0) ? -1 : ring(s - 1);
+  int64_t rc = end;
+  if (s < n) {
+    const uint32_t idx = sval[s];
+    s_hi[s] = u_hi[idx];
+    s_lo[s] = u_lo[idx];
+    const int64_t k = skey[s];
+    rc = (k >= npix) ? end : ring_of_key(ns, lg, k);
+  }
+  int64_t rp = __shfl_up_sync(0xffffffffu, rc, 1);
+  if (lane == 0) {
+    rp = -1;
+    if (s > 0 && s - 1 < n) {
+      const int64_t k = skey[s - 1];
+      rp = (k >= npix) ? end : ring_of_key(ns, lg, k);
+    }
+  }
+  if (s > n) return;
   for (int64_t i = rp + 1; i <= rc; ++i) ring_off[i] = (int32_t)s;
 }
 
@@ -367,6 +461,12 @@ cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int6
   return cudaGetLastError();
 }
 
+cudaError_t unit_vectors(const double* lon, const double* lat, int64_t n, double* out,
+                         cudaStream_t s) {
+  if (n > 0) k_unit_vectors<<<ceil_div(n, 256), 256, 0, s>>>(lon, lat, n, out);
+  return cudaGetLastError();
+}
+
 void tiling_free(Tiling& t, cudaStream_t s) {
   dfree(t.chi, s);
   dfree(t.clo, s);
@@ -431,21 +531,26 @@ static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
   dfree(g->val, s);
   dfree(g->s_hi, s);
   dfree(g->s_lo, s);
+  dfree(g->u_hi, s);
+  dfree(g->u_lo, s);
   g->cap_n = 0;
   cudaError_t e;
   if ((e = dalloc(&g->key, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->val, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->s_hi, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->s_lo, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->u_hi, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->u_lo, (size_t)n, s)) != cudaSuccess) return e;
   g->cap_n = (size_t)n;
   return cudaSuccess;
 }
 
-cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, int64_t n) {
+cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const float* weights,
+                         int64_t n) {
   cudaError_t e = ensure_samples(g, n);
   if (e != cudaSuccess) return e;
-  k_sample_keys<<<ceil_div(n, 256), 256, 0, g->stream>>>(g->nside, lon, lat, n, g->key, g->val,
-                                                         g->d_err);
+  k_sample_keys<<<ceil_div(n, 256), 256, 0, g->stream>>>(g->nside, lon, lat, weights, n, g->key,
+                                                         g->val, g->u_hi, g->u_lo, g->d_err);
   g->n_launches += 1;
   return cudaGetLastError();
 }
@@ -461,10 +566,14 @@ cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
                             const float* weights, int64_t n, Tiling& t) {
   cudaStream_t s = g->stream;
   const int64_t ns = g->nside;
-  k_sample_gather<<<ceil_div(n, 256), 256, 0, s>>>(ns, g->sorted_key, g->sorted_val, lon, lat,
-                                                   weights, n, g->s_hi, g->s_lo, g->d_err);
-  k_ring_off<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, g->sorted_key, n, g->ring_off);
-  g->n_launches += 2;
+  int lg = -1;
+  if ((ns & (ns - 1)) == 0)
+    for (lg = 0; ((int64_t)1 << lg) < ns; ++lg) {
+    }
+  k_sample_gather<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, lg, g->sorted_key, g->sorted_val,
+                                                       g->u_hi, g->u_lo, n, g->s_hi, g->s_lo,
+                                                       g->ring_off);
+  g->n_launches += 1;
   if (t.n_tiles > 0) {
     const int warps = 8;
     k_tile_ranges<<<ceil_div(t.n_tiles, warps), 32 * warps, 0, s>>>(

@@ -161,6 +161,15 @@ class Gridder:
             pass
 
 
+def unit_vectors(lon, lat, stream=None):
+    """Unit vectors [n, 3] (float64) of directions, as the gridder evaluates them."""
+    lon = _dev_f64(lon, "cuda")
+    lat = _dev_f64(lat, "cuda")
+    out = torch.empty((lon.numel(), 3), device=lon.device, dtype=torch.float64)
+    C.cg_unit_vectors(_ptr(lon), _ptr(lat), int(lon.numel()), _ptr(out), _stream_handle(stream))
+    return out
+
+
 def ang2pix_ring(nside: int, lon, lat, stream=None):
     """RING HEALPix index of each direction (int64 tensor, -1 if invalid)."""
     lon = _dev_f64(lon, "cuda")

@@ -101,3 +101,32 @@ def test_sort_and_ring_offsets_bit_exact(case):
     uniq, off = oracle.csr(pix)
     assert off[-1] == wl.n_samples and uniq.size <= wl.n_samples
     g.close()
+
+
+def test_unit_vectors_double_float():
+    """Sample unit vectors (double-float sine/cosine on the FP32 pipes) against
+    the FP64 definition: |error| <= 1e-13 per component, including quadrant
+    and table-interval boundaries, large longitudes and the poles."""
+    from paper_1604_06667_gb300 import unit_vectors
+    rng = np.random.Generator(np.random.PCG64(4242))
+    n = 200_000
+    lon = np.concatenate([rng.uniform(-1080, 1080, n),
+                          np.array([0.0, -0.0, 45.0, -45.0, 90.0, 135.0, 180.0, 225.0, 270.0,
+                                    315.0, 360.0, 1e-12, -1e-12, 44.999999999, 45.000000001,
+                                    0.5 * 180 / math.pi / 64, 1.5 * 180 / math.pi / 64,
+                                    720.0, -720.0, 1e6 + 0.123]),
+                          # table-interval edges j/64 +- 1/128 rad in degrees
+                          np.degrees((np.arange(-52, 53) + 0.5) / 64.0)])
+    lat = np.concatenate([np.degrees(np.arcsin(rng.uniform(-1, 1, n))),
+                          np.array([0.0, 90.0, -90.0, 89.9999999, -89.9999999, 45.0, -45.0,
+                                    1e-300, 30.0, 60.0, 0.0, 0.0, 0.0, 10.0, -10.0, 20.0,
+                                    20.0, 0.0, 0.0, 5.0]),
+                          np.clip(np.degrees((np.arange(-52, 53) + 0.5) / 64.0), -90, 90)])
+    got = unit_vectors(lon, lat).cpu().numpy()
+    # reduce the longitude in degrees first (exact), as radians(1e6 deg) alone
+    # would carry an FP64 rounding error of ~1e-12 rad
+    b, l = np.radians(lat), np.radians(np.fmod(lon, 360.0))
+    ref = np.stack([np.cos(b) * np.cos(l), np.cos(b) * np.sin(l), np.sin(b)], axis=1)
+    err = np.abs(got - ref).max()
+    assert err <= 1e-13, err
+    assert np.abs(np.linalg.norm(got, axis=1) - 1.0).max() <= 2e-13

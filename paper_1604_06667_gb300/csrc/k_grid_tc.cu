@@ -281,6 +281,78 @@ __device__ __forceinline__ void advance(const TcArgs& a, int64_t n_items, int64_
   }
 }
 
+// Constants of the weight evaluation (per kernel launch).
+struct PairConst {
+  float q1, q2, q4;          // exponent coefficients (log2 e folded in)
+  float c2_in, c2_out;       // guard band of the support cut (chord^2)
+  float c2_mid, c2_half;     // band test: |c2 - mid| <= half
+};
+
+// N weights omega w(p, k) of this thread's target against candidates cand[0
+// .. N-1] (tile-relative vectors, w = log2 omega) into w[], zero beyond the
+// support; pairs whose cut falls inside the guard band are decided from the
+// FP64 coordinates.  np counts the pairs with d <= r.
+template <int N, int KT, bool BIG>
+__device__ __forceinline__ void eval_pairs(const float4* cand, const uint32_t* cidx, float4 at,
+                                           float4 f1, float4 f2, const PairConst& P,
+                                           const TcArgs& a, int64_t slot, float* w,
+                                           unsigned& np) {
+  float bm = INFINITY;     // distance of the nearest c2 to the band centre
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float4 cb = cand[k];
+    const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
+    const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float e;
+    if (BIG) {
+      const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+      const float d2 = d * d;
+      if (KT == CG_GAUSS1D) {
+        e = fmaf(P.q1, d2, cb.w);
+      } else {
+        const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+        const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+        const float s2 = fmaf(ap, ap, bp * bp);
+        const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+        e = fmaf(fmaf(P.q1 * ap, ap, P.q4 * bp * bp), ratio, cb.w);
+      }
+    } else if (KT == CG_GAUSS1D) {
+      // d^2 = c^2 (1 + c^2/12) (the c^4/90 term is below FP32 here), folded
+      // into the exponent, plus log2(omega)
+      e = fmaf(c2, fmaf(c2, P.q2, P.q1), cb.w);
+    } else {
+      // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
+      const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+      const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+      const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
+      e = fmaf(fmaf(P.q1 * ap, ap, P.q4 * bp * bp), ratio, cb.w);
+    }
+    const float wk = ex2_approx(e);
+    const bool in = c2 <= P.c2_out;
+    w[k] = in ? wk : 0.f;
+    np += in ? 1u : 0u;
+    bm = fminf(bm, fabsf(c2 - P.c2_mid));
+  }
+  // rare: decide pairs inside the guard band from the FP64 coordinates
+  if (__any_sync(0xffffffffu, bm <= P.c2_half)) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const float4 cb = cand[k];   // recomputed: cheaper than keeping N values live
+      const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
+      const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (c2 >= P.c2_in && c2 <= P.c2_out) {
+        const uint32_t idx = cidx[k];
+        const double2 tl = a.tll[slot];
+        const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+        if (!(d <= a.kd.r_rad)) {
+          w[k] = 0.f;
+          --np;
+        }
+      }
+    }
+  }
+}
+
 template <int KT, bool SPLIT, bool BIG>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ CUtensorMap tmap,
                                                          TcArgs a) {
@@ -485,12 +557,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int part_cols = cp / (kWW / 4);     // epilogue columns of this warp
     const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
-    const float q1 = a.kd.k1, q2 = a.kd.k1 * (1.f / 12.f);
-    const float q4 = a.kd.k2;
-    const float c2_in = a.kd.c2_in, c2_out = a.kd.c2_out;
+    PairConst P;
+    P.q1 = a.kd.k1;
+    P.q2 = a.kd.k1 * (1.f / 12.f);
+    P.q4 = a.kd.k2;
+    P.c2_in = a.kd.c2_in;
+    P.c2_out = a.kd.c2_out;
     // a pair is inside the guard band iff |c2 - mid| <= half (with slack)
-    const float c2_mid = 0.5f * (c2_in + c2_out);
-    const float c2_half = 0.5f * (c2_out - c2_in) * 1.001f + 1e-30f;
+    P.c2_mid = 0.5f * (P.c2_in + P.c2_out);
+    P.c2_half = 0.5f * (P.c2_out - P.c2_in) * 1.001f + 1e-30f;
     uint32_t q = 0, tq = 0;
     unsigned npair = 0;
     for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
@@ -520,90 +595,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           break;
         }
         // ---- 2 x 8 weights of this thread's row, branch-free ----
+        // lanes 0-15 test one candidate each against the quarter's reach;
+        // a group of 8 with none in reach is skipped, two live groups are
+        // evaluated as one 16-pair block (more independent work in flight)
+        const int kb = st * kK + grp * 16;
+        bool reach = false;
+        if (lane < 16) reach = S.reach[(st * 4 + quarter) * kK + grp * 16 + lane] <= reach2;
+        const uint32_t live = __ballot_sync(0xffffffffu, reach);
+        float w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = 0.f;
+        if ((live & 0xffu) && (live & 0xff00u)) {
+          eval_pairs<16, KT, BIG>(S.cand + kb, S.cidx + kb, at, f1, f2, P, a, slot, w, np_item);
+        } else if (live & 0xffu) {
+          eval_pairs<8, KT, BIG>(S.cand + kb, S.cidx + kb, at, f1, f2, P, a, slot, w, np_item);
+        } else if (live & 0xff00u) {
+          eval_pairs<8, KT, BIG>(S.cand + kb + 8, S.cidx + kb + 8, at, f1, f2, P, a, slot, w + 8,
+                                 np_item);
+        }
         uint32_t packed[8], packed_lo[8];
         float part = 0.f;
 #pragma unroll
-        for (int gi = 0; gi < kGPW; ++gi) {
-          const int g = grp * kGPW + gi;
-          const int kb = st * kK + g * 8;
-          bool reach = false;
-          if (lane < 8) reach = S.reach[(st * 4 + quarter) * kK + g * 8 + lane] <= reach2;
-          const bool grp_live = __any_sync(0xffffffffu, reach);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            packed[gi * 4 + j] = 0u;
-            packed_lo[gi * 4 + j] = 0u;
-          }
-          if (!grp_live) continue;
-          float w[8], c2k[8];
-          float bm = INFINITY;     // distance of the nearest c2 to the band centre
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float4 cb = S.cand[kb + k];
-            const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
-            const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float e;
-            if (BIG) {
-              const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
-              const float d2 = d * d;
-              if (KT == CG_GAUSS1D) {
-                e = fmaf(q1, d2, cb.w);
-              } else {
-                const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-                const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-                const float s2 = fmaf(ap, ap, bp * bp);
-                const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
-                e = fmaf(fmaf(q1 * ap, ap, q4 * bp * bp), ratio, cb.w);
-              }
-            } else if (KT == CG_GAUSS1D) {
-              // d^2 = c^2 (1 + c^2/12) (the c^4/90 term is below FP32 here),
-              // folded into the exponent, plus log2(omega)
-              e = fmaf(c2, fmaf(c2, q2, q1), cb.w);
-            } else {
-              // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
-              const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-              const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-              const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
-              e = fmaf(fmaf(q1 * ap, ap, q4 * bp * bp), ratio, cb.w);
-            }
-            const float wk = ex2_approx(e);
-            const bool in = c2 <= c2_out;
-            w[k] = in ? wk : 0.f;
-            np_item += in ? 1u : 0u;
-            bm = fminf(bm, fabsf(c2 - c2_mid));
-            c2k[k] = c2;
-          }
-          // rare: decide pairs inside the guard band from the FP64 coordinates
-          if (__any_sync(0xffffffffu, bm <= c2_half)) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (c2k[k] >= c2_in && c2k[k] <= c2_out) {
-                const uint32_t idx = S.cidx[kb + k];
-                const double2 tl = a.tll[slot];
-                const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
-                if (!(d <= a.kd.r_rad)) {
-                  w[k] = 0.f;
-                  --np_item;
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            part += w[2 * j] + w[2 * j + 1];
-            if (SPLIT) {
-              // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
-              // truncation), w_lo = w - w_hi is exact in FP32, then rounded
-              const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
-              const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
-              packed[gi * 4 + j] = __byte_perm(u0, u1, 0x7632);
-              const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
-                                                              w[2 * j + 1] - __uint_as_float(u1));
-              packed_lo[gi * 4 + j] = *reinterpret_cast<const uint32_t*>(&l2);
-            } else {
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
-              packed[gi * 4 + j] = *reinterpret_cast<const uint32_t*>(&b2);
-            }
+        for (int j = 0; j < 8; ++j) {
+          part += w[2 * j] + w[2 * j + 1];
+          if (SPLIT) {
+            // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
+            // truncation), w_lo = w - w_hi is exact in FP32, then rounded
+            const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
+            const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
+            packed[j] = __byte_perm(u0, u1, 0x7632);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
+                                                            w[2 * j + 1] - __uint_as_float(u1));
+            packed_lo[j] = *reinterpret_cast<const uint32_t*>(&l2);
+          } else {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
+            packed[j] = *reinterpret_cast<const uint32_t*>(&b2);
+            packed_lo[j] = 0u;
           }
         }
         // Kahan accumulation of the chunk partial into the weight map

@@ -13,7 +13,8 @@ plain-numpy helpers that follow the paper's definitions:
   lookup scheme (optionally with the ring-shifted disc of Eq. 4-5).
 * Sect. 3.5: ``nside_for_resolution`` -- the hpx-max-resolution rule.
 * Adjoint and d/dsigma of the normalised operator: ``degrid_bruteforce``,
-  ``dsigma_bruteforce``.
+  ``dsigma_bruteforce``; the dense operator ``operator_matrix`` and the
+  gradient-descent map-making loop ``mapmaking_gd`` built on them.
 """
 from __future__ import annotations
 
@@ -314,3 +315,41 @@ def dsigma_bruteforce(lon_t, lat_t, lon_s, lat_s, data, k: Kernel, omega=None) -
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Map making by gradient descent on the adjoint (plain numpy, FP64)
+# ---------------------------------------------------------------------------
+def operator_matrix(lon_t, lat_t, lon_s, lat_s, k: Kernel, omega=None) -> np.ndarray:
+    """Dense normalised gridding operator G [P, N] with R = G D (Eq. 3):
+    G[p, n] = omega_n w_pn / W_p, zero rows where W_p = 0.  Built by gridding
+    the identity (data = the N x N unit matrix), so it is the brute-force
+    gridder's own operator.  Small problems only (N channels)."""
+    N = np.asarray(lon_s).size
+    res = grid_bruteforce(lon_t, lat_t, lon_s, lat_s, np.eye(N), k, omega)
+    return np.nan_to_num(res.out, nan=0.0)
+
+
+def mapmaking_gd(G: np.ndarray, data, steps: int, alpha: float | None = None):
+    """Gradient descent on L(m) = 1/2 ||G^T m - D||^2 (the map m [P, C] whose
+    adjoint interpolation G^T m reproduces the samples D [N, C]).
+
+    Step alpha = 1 / max_n sum_p G[p, n] (the largest column sum of G): with
+    unit row sums (Eq. 3 normalisation) ||G G^T||_2 <= ||G||_inf ||G||_1 =
+    max column sum, so the loss cannot increase.  Starts from m = 0.
+    Returns (m, losses[steps + 1]) with losses[k] the loss before step k."""
+    G = np.asarray(G, dtype=np.float64)
+    D = np.asarray(data, dtype=np.float64)
+    if D.ndim == 1:
+        D = D[:, None]
+    if alpha is None:
+        alpha = 1.0 / G.sum(axis=0).max()
+    m = np.zeros((G.shape[0], D.shape[1]))
+    losses = []
+    for _ in range(steps):
+        r = G.T @ m - D
+        losses.append(0.5 * float(np.sum(r * r)))
+        m = m - alpha * (G @ r)
+    r = G.T @ m - D
+    losses.append(0.5 * float(np.sum(r * r)))
+    return m, np.array(losses), alpha

@@ -115,6 +115,11 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params,
  *   data_dtype        CG_F32 or CG_BF16.
  *   weights           device, [n_samples] float32 >= 0, or NULL for unit weights.
  *   n_samples         0 .. 2^31-1 (0 is a no-op).
+ * lon_deg = lat_deg = NULL (and weights = NULL) grids new channel data for the
+ * samples of the previous add, reusing its sample index (keys, sort, ranges);
+ * n_samples must then equal that add's count, and the previous add must come
+ * after the last cg_set_kernel (else CG_EINVAL).  The library keeps its own
+ * FP64 copy of the coordinates, so the caller's earlier arrays may be gone.
  * Asynchronous.  Non-finite or |lat| > 90 coordinates are reported by the
  * next synchronising call as CG_EINVAL. */
 cg_status cg_grid_add(cg_grid* g, const double* lon_deg, const double* lat_deg,
@@ -203,6 +208,42 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
  * Asynchronous on `stream`; CG_EINVAL for n < 0 or a null pointer. */
 cg_status cg_unit_vectors(const double* lon_deg, const double* lat_deg, int64_t n, double* xyz,
                           void* stream);
+
+/* Adjoint of the normalised gridding operator (paper Eq. 1-3 read as a
+ * linear map R = G D with G[p][n] = omega_n w_pn / W_p): degridding,
+ *   out[n][c] = sum_p G[p][n] map[p][c],
+ * for the samples of the last add (its sample index is reused; the target
+ * side uses a RING index of the targets built on the first call after
+ * cg_set_kernel).  The gradient of a loss L(R) with respect to the data is
+ * cg_degrid of dL/dR.
+ *   map          device float32 [n_targets][C] (user order).
+ *   map_weights  device float32 [n_targets]: W_p of the operator (the
+ *                out_weights of the gridding call), or NULL for the handle's
+ *                accumulated weight map (CG_ESTATE if a one-shot call left
+ *                none).  Targets with W_p <= 0 contribute nothing.
+ *   out          device float32 [n][C] in the add's sample order (samples
+ *                with invalid coordinates get 0).
+ *   n            must equal the last add's n_samples.
+ * Deterministic (a gather: each sample's sum has a fixed order).
+ * Asynchronous; CG_ESTATE without a previous add, CG_EINVAL on bad arguments. */
+cg_status cg_degrid(cg_grid* g, const float* map, const float* map_weights, float* out,
+                    int64_t n);
+
+/* Derivative of the normalised map with respect to the kernel width, for the
+ * circular gauss1d kernel with the support radius held fixed:
+ *   dR_pc/dsigma = (sum_n omega_n w'_pn D_nc - R_pc sum_n omega_n w'_pn) / W_p,
+ *   w' = dw/dsigma = w d^2 / sigma^3     (d, sigma in degrees),
+ * for the samples of the last add and the channel data `data` (the FP32
+ * CUDA-core gridder is run with w and with w').
+ *   data       device [n_samples][C], CG_F32 or CG_BF16 (data_dtype).
+ *   grad_out   device float32 [n_targets][C] upstream gradient dL/dR, or NULL.
+ *   dR         device float32 [n_targets][C] (user order), or NULL; NaN where
+ *              W_p = 0.
+ *   dsigma     device float64 scalar: sum_pc grad_out[p][c] dR[p][c] (W_p > 0
+ *              targets; deterministic FP64 reduction), or NULL (needs grad_out).
+ * CG_EINVAL for gauss2d kernels.  Asynchronous. */
+cg_status cg_grid_dsigma(cg_grid* g, const void* data, int32_t data_dtype, const float* grad_out,
+                         float* dR, double* dsigma);
 
 /* Copy out the sample index built by the last cg_grid_add (the sorted
  * replacement for the paper's hash tables, Sect. 3.4):

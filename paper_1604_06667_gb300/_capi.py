@@ -58,6 +58,8 @@ SIGNATURES = {
     "cg_get_info": [_vp, ctypes.POINTER(CgInfo)],
     "cg_ang2pix_ring": [_i32, _vp, _vp, _i64, _vp, _vp],
     "cg_unit_vectors": [_vp, _vp, _i64, _vp, _vp],
+    "cg_degrid": [_vp, _vp, _vp, _vp, _i64],
+    "cg_grid_dsigma": [_vp, _vp, _i32, _vp, _vp, _vp],
     "cg_grid_export_index": [_vp, _vp, _vp, _vp, _i64],
     "cg_set_timing": [_vp, _i32],
     "cg_read_timing": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)],
@@ -115,6 +117,8 @@ cg_sync = _call("cg_sync")
 cg_get_info = _call("cg_get_info")
 cg_ang2pix_ring = _call("cg_ang2pix_ring")
 cg_unit_vectors = _call("cg_unit_vectors")
+cg_degrid = _call("cg_degrid")
+cg_grid_dsigma = _call("cg_grid_dsigma")
 cg_grid_export_index = _call("cg_grid_export_index")
 cg_set_timing = _call("cg_set_timing")
 cg_read_timing = _call("cg_read_timing")

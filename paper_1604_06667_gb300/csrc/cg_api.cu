@@ -110,7 +110,26 @@ void free_all(cg_grid* g) {
   dfree(g->s_lo, s);
   dfree(g->u_hi, s);
   dfree(g->u_lo, s);
+  dfree(g->s_ll, s);
   dfree(g->ring_off, s);
+  dfree(g->tix_key, s);
+  dfree(g->tix_val, s);
+  dfree(g->tix_uhi, s);
+  dfree(g->tix_ulo, s);
+  dfree(g->tix_hi, s);
+  dfree(g->tix_lo, s);
+  dfree(g->tix_ring_off, s);
+  dfree(g->tix_invw, s);
+  if (g->tix_sw.keys_alt) cudaFreeAsync(g->tix_sw.keys_alt, s);
+  g->tix_sw.keys_alt = nullptr;
+  dfree(g->tix_sw.vals_alt, s);
+  dfree(g->tix_sw.hist, s);
+  dfree(g->tix_sw.totals, s);
+  dfree(g->ds_num, s);
+  dfree(g->ds_w, s);
+  dfree(g->ds_num0, s);
+  dfree(g->ds_w0, s);
+  dfree(g->ds_part, s);
   dfree(g->acc_num, s);
   dfree(g->acc_w, s);
   dfree(g->d_err, s);
@@ -152,7 +171,16 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
     return fail(CG_EINVAL, "%s: data_dtype must be CG_F32 or CG_BF16", where);
   if (n < 0 || n > 0x7fffffffLL) return fail(CG_EINVAL, "%s: n_samples out of range", where);
   if (n == 0) return CG_OK;
-  if (!lon || !lat || !data) return fail(CG_EINVAL, "%s: null coordinate or data pointer", where);
+  // lon = lat = NULL: the samples (and weights) of the previous add, whose
+  // sample index is reused; only the channel data are new
+  const bool reuse = !lon && !lat;
+  if (reuse && (!g->index_valid || n != g->last_n || weights))
+    return fail(CG_EINVAL,
+                "%s: lon = lat = NULL reuses the previous add's samples: needs a previous add "
+                "since cg_set_kernel with the same n_samples and weights = NULL",
+                where);
+  if ((!reuse && (!lon || !lat)) || !data)
+    return fail(CG_EINVAL, "%s: null coordinate or data pointer", where);
   const bool tc = use_tc(g, dtype, data);
   if (tc && !tc_supported(g, dtype, data))
     return fail(CG_EINVAL,
@@ -162,20 +190,30 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
   CG_CUDA(cudaSetDevice(g->device), where);
   Tiling& t = tc ? g->t128 : g->t64;
   cudaEvent_t t0 = tmark(g);
-  CG_CUDA(samples_keys(g, lon, lat, weights, n), where);
+  if (!reuse) {
+    g->index_valid = false;
+    CG_CUDA(samples_keys(g, lon, lat, weights, n), where);
+  }
   cudaEvent_t t1 = tmark(g);
-  CG_CUDA(samples_sort(g, n), where);
+  if (!reuse) CG_CUDA(samples_sort(g, n), where);
   cudaEvent_t t2 = tmark(g);
-  CG_CUDA(samples_prepare(g, lon, lat, weights, n, t), where);
+  if (!reuse) {
+    CG_CUDA(samples_prepare(g, n), where);
+    g->index_gen += 1;
+    g->index_valid = true;
+  }
+  if (t.ranges_gen != g->index_gen) {
+    CG_CUDA(tiles_ranges(g, t), where);
+    t.ranges_gen = g->index_gen;
+  }
   cudaEvent_t t3 = tmark(g);
   if (tc) {
     const bool fuse = out != nullptr && g->acc_empty;
     const int mode = fuse ? 2 : (g->acc_empty ? 0 : 1);
-    CG_CUDA(grid_tiles_tc(g, data, lon, lat, mode, out, out_w, g->path != CG_PATH_TC_FAST),
-            where);
+    CG_CUDA(grid_tiles_tc(g, data, mode, out, out_w, g->path != CG_PATH_TC_FAST), where);
     if (fused) *fused = fuse;
   } else {
-    CG_CUDA(grid_tiles_f32(g, data, dtype, lon, lat), where);
+    CG_CUDA(grid_tiles_f32(g, data, dtype), where);
   }
   cudaEvent_t t4 = tmark(g);
   tstage(g, 0, t0, t1);
@@ -294,6 +332,10 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
   if (kernel_type == CG_GAUSS2D) CG_CUDA(targets_set_axes(g, pa), "cg_set_kernel");
   CG_CUDA(tiles_query(g, g->t64), "cg_set_kernel");
   CG_CUDA(tiles_query(g, g->t128), "cg_set_kernel");
+  // nside and tiles may have changed: the sample and target indices are stale
+  g->index_valid = false;
+  g->t64.ranges_gen = g->t128.ranges_gen = -1;
+  g->tix_valid = false;
   cg_status st = zero_acc(g);
   if (st != CG_OK) return st;
   g->kernel_set = true;
@@ -440,6 +482,48 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
     return fail(CG_EINVAL, "cg_ang2pix_ring: null pointer");
   CG_CUDA(ang2pix_export(nside, lon_deg, lat_deg, n, pix, static_cast<cudaStream_t>(stream)),
           "cg_ang2pix_ring");
+  return CG_OK;
+}
+
+cg_status cg_degrid(cg_grid* g, const float* map, const float* map_weights, float* out,
+                    int64_t n) {
+  g_last_error.clear();
+  const char* where = "cg_degrid";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (!g->index_valid)
+    return fail(CG_ESTATE, "%s: no sample index: call cg_grid_add (or oneshot) first", where);
+  if (n != g->last_n)
+    return fail(CG_EINVAL, "%s: n (%lld) must equal the last add's n_samples (%lld)", where,
+                (long long)n, (long long)g->last_n);
+  if (!map || !out) return fail(CG_EINVAL, "%s: null map or out pointer", where);
+  if (!map_weights && g->acc_empty)
+    return fail(CG_ESTATE,
+                "%s: no accumulated weight map (one-shot calls leave none): pass map_weights",
+                where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  CG_CUDA(grid_degrid(g, map, map_weights, out), where);
+  return CG_OK;
+}
+
+cg_status cg_grid_dsigma(cg_grid* g, const void* data, int32_t data_dtype, const float* grad_out,
+                         float* dR, double* dsigma) {
+  g_last_error.clear();
+  const char* where = "cg_grid_dsigma";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (g->kernel_type != CG_GAUSS1D)
+    return fail(CG_EINVAL, "%s: d/dsigma is defined for the circular gauss1d kernel", where);
+  if (!g->index_valid)
+    return fail(CG_ESTATE, "%s: no sample index: call cg_grid_add (or oneshot) first", where);
+  if (data_dtype != CG_F32 && data_dtype != CG_BF16)
+    return fail(CG_EINVAL, "%s: data_dtype must be CG_F32 or CG_BF16", where);
+  if (!data) return fail(CG_EINVAL, "%s: null data pointer", where);
+  if (dsigma && !grad_out)
+    return fail(CG_EINVAL, "%s: the scalar dsigma needs grad_out", where);
+  if (!dR && !dsigma) return fail(CG_EINVAL, "%s: nothing to compute (dR and dsigma NULL)", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  CG_CUDA(grid_dsigma(g, data, data_dtype, grad_out, dR, dsigma), where);
   return CG_OK;
 }
 

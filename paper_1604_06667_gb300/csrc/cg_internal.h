@@ -36,6 +36,7 @@ struct KernelDev {        // kernel constants used by the gridder
   float c2_cut;           // chord^2 of the support radius
   double r_rad;           // support radius (FP64 guard-band decision)
   int big_support;        // 1 if the chord series for d^2 is not accurate enough
+  float dscale;           // 0; else the weight is w d^2 dscale (d/dsigma pass)
 };
 
 struct Tiling {           // geometry of one tiling of the targets
@@ -56,6 +57,7 @@ struct Tiling {           // geometry of one tiling of the targets
   // tile centre in FP32 with the radius as a chord
   double4* sub64 = nullptr;       // [n_tiles * 4]
   float4* subf = nullptr;         // [n_tiles * 4]
+  int64_t ranges_gen = -1;        // sample index the per-add ranges belong to
 };
 
 struct SortWork {         // radix-sort scratch
@@ -105,9 +107,33 @@ struct cg_grid {
   float4* s_lo = nullptr;         // [cap_n] unit vector lo
   float4* u_hi = nullptr;         // [cap_n] input order: unit vector hi, w = omega
   float4* u_lo = nullptr;         // [cap_n] input order: unit vector lo
+  double2* s_ll = nullptr;        // [cap_n] input order: FP64 lon/lat (guard-band decisions)
   int32_t* ring_off = nullptr;    // [4*nside + 1]
   int64_t last_n = 0;
   int64_t total_n = 0;
+  bool index_valid = false;       // the sample index of the last add is usable
+  int64_t index_gen = 0;          // bumped by every new sample index
+
+  // target index of the degridder (RING keys of the targets, sorted; built on
+  // the first cg_degrid after cg_set_kernel)
+  bool tix_valid = false;
+  uint32_t* tix_key = nullptr;    // [n_slots] RING key per slot (npix: empty slot)
+  uint32_t* tix_val = nullptr;    // [n_slots] slot
+  uint32_t* tix_skey = nullptr;   // sorted keys (into tix_key or tix_sw)
+  uint32_t* tix_sslot = nullptr;  // slot of each sorted key
+  float4* tix_uhi = nullptr;      // [n_slots] slot order unit vector hi
+  float4* tix_ulo = nullptr;
+  float4* tix_hi = nullptr;       // [n_slots] sorted order
+  float4* tix_lo = nullptr;
+  int32_t* tix_ring_off = nullptr;  // [4 nside + 1]
+  float* tix_invw = nullptr;      // [n_slots] 1 / W of the operator being transposed
+  cg::SortWork tix_sw;
+  // scratch accumulators of cg_grid_dsigma (w' = dw/dsigma pass)
+  float* ds_num = nullptr;        // [slots][C]
+  float2* ds_w = nullptr;         // [slots]
+  float* ds_num0 = nullptr;       // [slots][C] (w pass)
+  float2* ds_w0 = nullptr;        // [slots]
+  double* ds_part = nullptr;      // per-block partial sums
 
   // accumulators (tile order)
   float* acc_num = nullptr;       // [slots][C]
@@ -155,26 +181,40 @@ cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const
 cudaError_t unit_vectors(const double* lon, const double* lat, int64_t n, double* out,
                          cudaStream_t s);
 cudaError_t samples_sort(cg_grid* g, int64_t n);
-cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
-                            const float* weights, int64_t n, Tiling& t);
+cudaError_t samples_prepare(cg_grid* g, int64_t n);
+int key_bits_for(int64_t ns);   // bits of a RING key at nside (incl. the invalid sentinel)
+// gather (hi, lo) records into sorted order and build ring offsets [4 ns + 1]
+cudaError_t sorted_gather(int64_t ns, const uint32_t* skey, const uint32_t* sval,
+                          const float4* u_hi, const float4* u_lo, int64_t n, float4* s_hi,
+                          float4* s_lo, int32_t* ring_off, cudaStream_t s);
+cudaError_t tiles_ranges(cg_grid* g, Tiling& t);
 cudaError_t tiles_query(cg_grid* g, Tiling& t);
 void tiling_free(Tiling& t, cudaStream_t s);
 cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t* ring_off,
                          int64_t n);
 
 // k_grid.cu -- the tile gridder (FP32 CUDA-core form).
-cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
-                           const double* lat);
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype);
+// the same into given accumulators; dscale != 0 evaluates w d^2 dscale
+// instead of w (the d/dsigma pass) and counts no pairs
+cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
+                              float2* acc_w, int accumulate, float dscale);
 // k_grid_tc.cu -- the tile gridder, BF16 tcgen05 form (TMEM accumulators).
 // mode 0: store into the accumulators, 1: add into them, 2: one-shot
 // normalised output in the caller's [P][C] layout (out, out_w).
 bool tc_supported(const cg_grid* g, int dtype, const void* data);
-cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
-                          int mode, float* out, float* out_w, int split);
+cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, float* out_w,
+                          int split);
 // k_noalloc.cu -- sample index on the library's static scratch array.
 cudaError_t sort_samples_noalloc(int nside, const double* lon, const double* lat, int64_t n,
                                  int64_t* sorted_pix, int64_t* perm, cudaStream_t s);
 // k_finalize.cu -- normalisation and output layout.
+// k_degrid.cu -- adjoint (degridding) and d/dsigma
+cudaError_t target_index_build(cg_grid* g);
+cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* out);
+cudaError_t grid_dsigma(cg_grid* g, const void* data, int dtype, const float* grad, float* dR,
+                        double* dsigma);
+
 cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w);
 
 // device allocation helper (stream ordered); returns cudaErrorMemoryAllocation on failure

@@ -40,8 +40,7 @@ struct GridArgs {
   const float4* s_hi;
   const float4* s_lo;
   const uint32_t* perm;
-  const double* lon;
-  const double* lat;
+  const double2* sll;   // FP64 lon/lat of each sample (input order, degrees)
   const void* data;
   int C;
   int vec4;  // data rows are 16-byte (f32) / 8-byte (bf16) aligned in groups of 4
@@ -247,11 +246,13 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
             ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
           }
           w = ex2_approx(ex) * sh.w;
+          if (a.kd.dscale != 0.f) w *= d2 * a.kd.dscale;   // dw/dsigma pass
           if (c2 >= a.kd.c2_in) {
             // guard band: decide d <= r in FP64 from the input coordinates
             const uint32_t idx = sh_idx[k];
             const double2 tl = a.tgt_ll[slot];
-            const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+            const double2 sl = a.sll[idx];
+            const double d = haversine_f64(tl.x, tl.y, sl.x, sl.y);
             if (!(d <= a.kd.r_rad)) w = -1.f;
           }
           if (w >= 0.f) ++npair; else w = 0.f;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     unsigned c = npair;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((tid & 31) == 0 && c) atomicAdd(a.pairs, (unsigned long long)c);
+    if ((tid & 31) == 0 && c && a.pairs) atomicAdd(a.pairs, (unsigned long long)c);
   }
   __syncthreads();
   if (kk0 == 0 && a.tgt_perm[slot] != 0xffffffffu) {
@@ -356,8 +357,12 @@ cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s
 
 }  // namespace
 
-cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double* lon,
-                           const double* lat) {
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype) {
+  return grid_tiles_f32_to(g, data, dtype, g->acc_num, g->acc_w, g->acc_empty ? 0 : 1, 0.f);
+}
+
+cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
+                              float2* acc_w, int accumulate, float dscale) {
   GridArgs a;
   a.tile_chi = g->t64.chi;
   a.tile_clo = g->t64.clo;
@@ -371,17 +376,18 @@ cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, const double
   a.s_hi = g->s_hi;
   a.s_lo = g->s_lo;
   a.perm = g->sorted_val;
-  a.lon = lon;
-  a.lat = lat;
+  a.sll = g->s_ll;
   a.data = data;
   a.C = g->C;
   const size_t esz = (dtype == CG_BF16) ? 2 : 4;
   a.vec4 = (g->C % 4 == 0) && ((reinterpret_cast<uintptr_t>(data) % (4 * esz)) == 0);
   a.kd = g->kdev;
-  a.acc_num = g->acc_num;
-  a.acc_w = g->acc_w;
-  a.accumulate = g->acc_empty ? 0 : 1;
-  a.pairs = g->d_pairs;
+  a.kd.dscale = dscale;
+  a.acc_num = acc_num;
+  a.acc_w = acc_w;
+  a.accumulate = accumulate;
+  // only the handle's own accumulation counts pairs (not the scratch passes)
+  a.pairs = (dscale != 0.f || acc_num != g->acc_num) ? nullptr : g->d_pairs;
   g->n_launches += 1;
   const int C = g->C;
   const int64_t nt = g->t64.n_tiles;

@@ -85,8 +85,7 @@ struct TcArgs {
   const float4* s_hi;
   const float4* s_lo;
   const uint32_t* sperm;
-  const double* lon;
-  const double* lat;
+  const double2* sll;   // FP64 lon/lat of each sample (input order, degrees)
   const __nv_bfloat16* data;
   int C;
   int cp;        // padded channels per slab (multiple of 64, <= 256)
@@ -343,7 +342,8 @@ __device__ __forceinline__ void eval_pairs(const float4* cand, const uint32_t* c
       if (c2 >= P.c2_in && c2 <= P.c2_out) {
         const uint32_t idx = cidx[k];
         const double2 tl = a.tll[slot];
-        const double d = haversine_f64(tl.x, tl.y, a.lon[idx], a.lat[idx]);
+        const double2 sl = a.sll[idx];
+        const double d = haversine_f64(tl.x, tl.y, sl.x, sl.y);
         if (!(d <= a.kd.r_rad)) {
           w[k] = 0.f;
           --np;
@@ -792,8 +792,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const double* lat,
-                          int mode, float* out, float* out_w, int split) {
+cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, float* out_w, int split) {
   const Tiling& t = g->t128;
   TcArgs a;
   a.chi = t.chi;
@@ -812,8 +811,7 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, const double* lon, const
   a.s_hi = g->s_hi;
   a.s_lo = g->s_lo;
   a.sperm = g->sorted_val;
-  a.lon = lon;
-  a.lat = lat;
+  a.sll = g->s_ll;
   a.data = static_cast<const __nv_bfloat16*>(data);
   a.C = g->C;
   const int slab = g->C < 256 ? g->C : 256;

@@ -13,145 +13,10 @@
 #include "cg_common.cuh"
 #include "cg_internal.h"
 #include "cg_trig.cuh"
+#include "cg_healpix.cuh"
 
 namespace cg {
 namespace {
-
-struct RingGeo {
-  int64_t count, first;
-  double z, phase;
-};
-
-__device__ __forceinline__ RingGeo ring_geo(int64_t ns, int64_t i) {
-  RingGeo r;
-  const double dns = (double)ns;
-  if (i < ns) {
-    r.count = 4 * i;
-    r.first = 2 * i * (i - 1);
-    r.z = 1.0 - (double)(i * i) / (3.0 * dns * dns);
-    r.phase = 0.5;
-  } else if (i <= 3 * ns) {
-    r.count = 4 * ns;
-    r.first = 2 * ns * (ns - 1) + (i - ns) * 4 * ns;
-    r.z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * dns);
-    r.phase = (((i - ns) & 1) == 0) ? 0.5 : 0.0;
-  } else {
-    const int64_t k = 4 * ns - i;
-    r.count = 4 * k;
-    r.first = 12 * ns * ns - 2 * k * (k + 1);
-    r.z = -(1.0 - (double)(k * k) / (3.0 * dns * dns));
-    r.phase = 0.5;
-  }
-  return r;
-}
-
-__device__ __forceinline__ double ring_colat(int64_t ns, int64_t i) {
-  if (i <= 0) return 0.0;
-  if (i >= 4 * ns) return kPi;
-  return acos(ring_geo(ns, i).z);
-}
-
-// Continuous ring coordinate of a direction with cos(colatitude) = z.
-__device__ __forceinline__ double ring_coord(int64_t ns, double z) {
-  const double dns = (double)ns;
-  if (fabs(z) <= 2.0 / 3.0) return dns * (2.0 - 1.5 * z);
-  if (z > 0.0) return dns * sqrt(3.0 * (1.0 - z));
-  return 4.0 * dns - dns * sqrt(3.0 * (1.0 + z));
-}
-
-// Widest longitude half-width of the disc (centre colatitude tc, radius R)
-// over the colatitude band [ta, tb]: -1 if the disc misses the band, >= pi if
-// it covers every longitude there.  The half-width at colatitude t solves
-// cos R = cos tc cos t + sin tc sin t cos(dphi); its widest point over t is
-// at cos t = cos tc / cos R (or at a band edge).
-__device__ double disc_halfwidth(double tc, double R, double ta, double tb) {
-  if (tb < tc - R || ta > tc + R) return -1.0;
-  if (ta <= 0.0 && tc <= R) return 4.0 * kPi;
-  if (tb >= kPi && tc + R >= kPi) return 4.0 * kPi;
-  const double st = sin(tc), ct = cos(tc), cr = cos(R);
-  if (st <= 0.0) return 4.0 * kPi;
-  double lo = fmax(ta, tc - R), hi = fmin(tb, tc + R);
-  lo = fmax(lo, 1e-300);
-  hi = fmin(hi, kPi - 1e-16);
-  double ts = (fabs(ct / cr) <= 1.0) ? acos(ct / cr) : lo;
-  ts = fmin(fmax(ts, lo), hi);
-  double xmin = 1e300;
-  const double cand[3] = {lo, hi, ts};
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const double x = (cr - ct * cos(cand[q])) / (st * sin(cand[q]));
-    xmin = fmin(xmin, x);
-  }
-  if (xmin <= -1.0) return 4.0 * kPi;
-  if (xmin > 1.0) return -1.0;
-  return acos(xmin);
-}
-
-// A disc on the sphere: colatitude, longitude (radians) and radius.
-struct Disc {
-  double tc, pc, R;
-};
-
-// Pixel ranges of ring i met by the union of nd discs (the hull of their
-// pixel intervals on the ring, a superset); writes up to 2 into out.
-__device__ int ring_ranges(int64_t ns, int64_t i, const Disc* discs, int nd, Range* out) {
-  const RingGeo g = ring_geo(ns, i);
-  const double dphi = 2.0 * kPi / (double)g.count;
-  const double ta = ring_colat(ns, i - 1), tb = ring_colat(ns, i + 1);
-  bool any = false, full = false;
-  double lo = 0.0, hi = 0.0;   // hull of [pc - W, pc + W], unwrapped near the first disc
-  for (int q = 0; q < nd && !full; ++q) {
-    const double hw = disc_halfwidth(discs[q].tc, discs[q].R, ta, tb);
-    if (hw < 0.0) continue;
-    const double W = hw + 0.5 * dphi + 1e-12;
-    if (W >= kPi) { full = true; break; }
-    double c = discs[q].pc;
-    if (any) {  // move c to within pi of the hull's first centre
-      const double ref = 0.5 * (lo + hi);
-      while (c - ref > kPi) c -= 2.0 * kPi;
-      while (ref - c > kPi) c += 2.0 * kPi;
-      lo = fmin(lo, c - W);
-      hi = fmax(hi, c + W);
-    } else {
-      lo = c - W;
-      hi = c + W;
-      any = true;
-    }
-  }
-  if (!any && !full) return 0;
-  int64_t jlo = 0, jhi = g.count - 1;
-  if (!full && hi - lo >= 2.0 * kPi) full = true;
-  if (!full) {
-    jlo = (int64_t)ceil(lo / dphi - g.phase);
-    jhi = (int64_t)floor(hi / dphi - g.phase);
-    if (jhi < jlo) return 0;
-    if (jhi - jlo + 1 >= g.count) full = true;
-  }
-  if (full) {
-    if (out) out[0] = Range{(int32_t)g.first, (int32_t)(g.first + g.count - 1), (int32_t)i, 0};
-    return 1;
-  }
-  int64_t a = jlo % g.count, b = jhi % g.count;
-  if (a < 0) a += g.count;
-  if (b < 0) b += g.count;
-  if (a <= b) {
-    if (out) out[0] = Range{(int32_t)(g.first + a), (int32_t)(g.first + b), (int32_t)i, 0};
-    return 1;
-  }
-  if (out) {
-    out[0] = Range{(int32_t)g.first, (int32_t)(g.first + b), (int32_t)i, 0};
-    out[1] = Range{(int32_t)(g.first + a), (int32_t)(g.first + g.count - 1), (int32_t)i, 0};
-  }
-  return 2;
-}
-
-__device__ __forceinline__ Disc make_disc(double4 c, double r_rad) {
-  Disc d;
-  d.tc = acos(fmin(1.0, fmax(-1.0, c.z)));
-  d.pc = atan2(c.y, c.x);
-  d.R = c.w + r_rad;
-  return d;
-}
 
 // One warp per tile; mode 0 counts ranges, mode 1 writes them.  With sub64
 // the tile's candidates are those of its four quarter discs (tighter than one
@@ -206,72 +71,6 @@ __global__ void k_tile_query(const double4* __restrict__ tc64,
   if (mode == 0 && lane == 0) counts[tile] = total;
 }
 
-__device__ __forceinline__ bool valid_coord(double lon, double lat) {
-  return isfinite(lon) && isfinite(lat) && lat >= -90.0 && lat <= 90.0;
-}
-
-// HEALPix RING index from an approximate z = sin(lat) (|error| ~1e-14):
-// the same decisions as ang2pix_ring_f64, each checked for a margin that the
-// FP64 evaluation's own rounding cannot cross; *ok = false when a value lies
-// within that margin of a decision boundary (then the exact FP64 routine
-// decides).  For nside <= 16384 a truncated quantity is at most 4 nside =
-// 65536 and FP64 and this evaluation differ by < 1e-9 there; the margin is
-// 1e-6.
-__device__ __forceinline__ int64_t ang2pix_ring_fast(int64_t ns, double lon_deg, double z,
-                                                     bool* ok) {
-  constexpr double M = 1e-6;
-  const double za = fabs(z);
-  const double phi = lon_fold_deg(lon_deg);
-  const double tt = phi * (1.0 / 90.0);
-  const double dns = (double)ns;
-  bool good = fabs(za - 2.0 / 3.0) > 1e-9;
-  int64_t pix;
-  if (za <= 2.0 / 3.0) {
-    const double u = dns * (0.5 + tt);
-    const double v = dns * (z * 0.75);
-    const double A = u - v, B = u + v;
-    const double fa = A - floor(A), fb = B - floor(B);
-    good = good && fa > M && fa < 1.0 - M && fb > M && fb < 1.0 - M;
-    const int64_t asc = (int64_t)A;
-    const int64_t dsc = (int64_t)B;
-    const int64_t k = ns + 1 + asc - dsc;
-    const int64_t odd = k & 1;
-    int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
-    j %= 4 * ns;
-    if (j < 0) j += 4 * ns;
-    pix = 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
-  } else {
-    const double ft = tt - floor(tt);
-    // near a pole sqrt(1 - za) magnifies the error of z: leave it to FP64
-    good = good && ft > 1e-12 && ft < 1.0 - 1e-12 && 1.0 - za > 1e-6;
-    const double x = dns * sqrt(3.0 * (1.0 - za));
-    const double P = ft * x, Q = (1.0 - ft) * x;
-    const double fp = P - floor(P), fq = Q - floor(Q);
-    good = good && fp > M && fp < 1.0 - M && fq > M && fq < 1.0 - M;
-    const int64_t a = (int64_t)P;
-    const int64_t b = (int64_t)Q;
-    const int64_t k = a + b + 1;
-    const double J = tt * (double)k;
-    const double fj = J - floor(J);
-    good = good && fj > M && fj < 1.0 - M;
-    int64_t j = (int64_t)J;
-    j %= 4 * k;
-    if (j < 0) j += 4 * k;
-    pix = (z > 0.0) ? 2 * k * (k - 1) + j : 12 * ns * ns - 2 * k * (k + 1) + j;
-  }
-  *ok = good;
-  return pix;
-}
-
-// RING index of a valid sample with z from the double-float sine; exact
-// FP64 fallback near decision boundaries.
-__device__ __forceinline__ int64_t ang2pix_ring_dual(int64_t ns, double lon, double lat,
-                                                     df32 sb) {
-  if (ns > 16384) return ang2pix_ring_f64(ns, lon, lat);
-  bool ok;
-  const int64_t p = ang2pix_ring_fast(ns, lon, (double)sb.hi + (double)sb.lo, &ok);
-  return ok ? p : ang2pix_ring_f64(ns, lon, lat);
-}
 
 __global__ void k_ang2pix_export(int64_t ns, const double* __restrict__ lon,
                                  const double* __restrict__ lat, int64_t n,
@@ -310,11 +109,12 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
                               const float* __restrict__ weights, int64_t n,
                               uint32_t* __restrict__ key, uint32_t* __restrict__ val,
                               float4* __restrict__ u_hi, float4* __restrict__ u_lo,
-                              unsigned* err) {
+                              double2* __restrict__ sll, unsigned* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double lo = lon[i], la = lat[i];
   val[i] = (uint32_t)i;
+  sll[i] = make_double2(lo, la);
   if (!valid_coord(lo, la)) {
     key[i] = (uint32_t)(12 * ns * ns);
     u_hi[i] = make_float4(4.f, 4.f, 4.f, 0.f);
@@ -339,14 +139,6 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
   u_lo[i] = make_float4(x.lo, y.lo, sb.lo, 0.f);
 }
 
-// Ring number of pixel p (RING scheme); the belt division by 4 ns is a
-// shift when nside is a power of two (log2 given, else -1).
-__device__ __forceinline__ int64_t ring_of_key(int64_t ns, int lg, int64_t p) {
-  const int64_t ncap = 2 * ns * (ns - 1);
-  if (p >= ncap && p < 12 * ns * ns - ncap)
-    return ns + (lg >= 0 ? ((p - ncap) >> (lg + 2)) : (p - ncap) / (4 * ns));
-  return ring_of_pix(ns, p);
-}
 
 // Sorted order: gather the unit vectors, and ring_off[i] = first sorted
 // position with ring >= i, i = 0 .. 4 ns (thread s writes the entries for
@@ -381,14 +173,6 @@ __global__ void k_sample_gather(int64_t ns, int lg, const uint32_t* __restrict__
   for (int64_t i = rp + 1; i <= rc; ++i) ring_off[i] = (int32_t)s;
 }
 
-__device__ __forceinline__ int32_t lower_bound_u32(const uint32_t* __restrict__ a, int32_t lo,
-                                                   int32_t hi, uint32_t v) {
-  while (lo < hi) {
-    const int32_t mid = lo + ((hi - lo) >> 1);
-    if (a[mid] < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 // One warp per tile: the sorted-sample interval [lo, hi) of each of the
 // tile's pixel ranges (binary search inside the range's ring), the number of
@@ -445,14 +229,14 @@ __global__ void k_export_ring(const int32_t* __restrict__ ro, int64_t m, int64_t
   if (i < m) out[i] = ro[i];
 }
 
+}  // namespace
+
 int key_bits_for(int64_t ns) {
   const uint64_t maxkey = (uint64_t)(12 * ns * ns);  // sentinel for invalid samples
   int b = 0;
   while (b < 32 && (maxkey >> b) != 0) ++b;
   return b;
 }
-
-}  // namespace
 
 cudaError_t ang2pix_export(int nside, const double* lon, const double* lat, int64_t n,
                            int64_t* pix, cudaStream_t s) {
@@ -533,6 +317,7 @@ static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
   dfree(g->s_lo, s);
   dfree(g->u_hi, s);
   dfree(g->u_lo, s);
+  dfree(g->s_ll, s);
   g->cap_n = 0;
   cudaError_t e;
   if ((e = dalloc(&g->key, (size_t)n, s)) != cudaSuccess) return e;
@@ -541,6 +326,7 @@ static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
   if ((e = dalloc(&g->s_lo, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->u_hi, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->u_lo, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->s_ll, (size_t)n, s)) != cudaSuccess) return e;
   g->cap_n = (size_t)n;
   return cudaSuccess;
 }
@@ -550,7 +336,8 @@ cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const
   cudaError_t e = ensure_samples(g, n);
   if (e != cudaSuccess) return e;
   k_sample_keys<<<ceil_div(n, 256), 256, 0, g->stream>>>(g->nside, lon, lat, weights, n, g->key,
-                                                         g->val, g->u_hi, g->u_lo, g->d_err);
+                                                         g->val, g->u_hi, g->u_lo, g->s_ll,
+                                                         g->d_err);
   g->n_launches += 1;
   return cudaGetLastError();
 }
@@ -562,26 +349,37 @@ cudaError_t samples_sort(cg_grid* g, int64_t n) {
                         &g->sorted_val);
 }
 
-cudaError_t samples_prepare(cg_grid* g, const double* lon, const double* lat,
-                            const float* weights, int64_t n, Tiling& t) {
-  cudaStream_t s = g->stream;
-  const int64_t ns = g->nside;
+cudaError_t sorted_gather(int64_t ns, const uint32_t* skey, const uint32_t* sval,
+                          const float4* u_hi, const float4* u_lo, int64_t n, float4* s_hi,
+                          float4* s_lo, int32_t* ring_off, cudaStream_t s) {
   int lg = -1;
   if ((ns & (ns - 1)) == 0)
     for (lg = 0; ((int64_t)1 << lg) < ns; ++lg) {
     }
-  k_sample_gather<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, lg, g->sorted_key, g->sorted_val,
-                                                       g->u_hi, g->u_lo, n, g->s_hi, g->s_lo,
-                                                       g->ring_off);
+  k_sample_gather<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, lg, skey, sval, u_hi, u_lo, n, s_hi,
+                                                       s_lo, ring_off);
+  return cudaGetLastError();
+}
+
+cudaError_t samples_prepare(cg_grid* g, int64_t n) {
+  cudaStream_t s = g->stream;
+  const int64_t ns = g->nside;
+  cudaError_t e = sorted_gather(ns, g->sorted_key, g->sorted_val, g->u_hi, g->u_lo, n, g->s_hi,
+                                g->s_lo, g->ring_off, s);
+  if (e != cudaSuccess) return e;
   g->n_launches += 1;
+  g->last_n = n;
+  return cudaGetLastError();
+}
+
+cudaError_t tiles_ranges(cg_grid* g, Tiling& t) {
   if (t.n_tiles > 0) {
     const int warps = 8;
-    k_tile_ranges<<<ceil_div(t.n_tiles, warps), 32 * warps, 0, s>>>(
+    k_tile_ranges<<<ceil_div(t.n_tiles, warps), 32 * warps, 0, g->stream>>>(
         t.ranges, t.range_off, t.n_tiles, g->ring_off, g->sorted_key, t.range_s, t.range_c,
         t.tile_cand);
     g->n_launches += 1;
   }
-  g->last_n = n;
   return cudaGetLastError();
 }
 

@@ -73,20 +73,28 @@ class Gridder:
         raise TypeError("data must be float32 or bfloat16")
 
     def _prep(self, lon, lat, data, weights):
-        lon = _dev_f64(lon, self.device)
-        lat = _dev_f64(lat, self.device)
+        """lon = lat = None: the samples of the previous add (its index is reused)."""
         data = torch.as_tensor(data, device=self.device)
         if data.dtype not in (torch.float32, torch.bfloat16):
             data = data.to(torch.float32)
+        if lon is None and lat is None:
+            data = data.reshape(-1, self.n_channels).contiguous()
+            return None, None, data, weights, int(data.shape[0])
+        lon = _dev_f64(lon, self.device)
+        lat = _dev_f64(lat, self.device)
         data = data.reshape(lon.numel(), self.n_channels).contiguous()
         if weights is not None:
             weights = torch.as_tensor(weights, device=self.device, dtype=torch.float32).contiguous()
-        return lon, lat, data, weights
+        self.index_gen = getattr(self, "index_gen", 0) + 1
+        self.n_samples = int(lon.numel())
+        return lon, lat, data, weights, int(lon.numel())
 
     def grid(self, lon, lat, data, weights=None):
-        lon, lat, data, weights = self._prep(lon, lat, data, weights)
+        """Accumulate (Eq. 1-2).  lon = lat = None grids new data for the samples
+        of the previous add, reusing its sample index."""
+        lon, lat, data, weights, n = self._prep(lon, lat, data, weights)
         C.cg_grid_add(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
-                      _ptr(weights), int(lon.numel()))
+                      _ptr(weights), n)
         self._keep = (lon, lat, data, weights)   # alive until the stream has consumed them
         return self
 
@@ -107,16 +115,53 @@ class Gridder:
 
     def grid_oneshot(self, lon, lat, data, weights=None, out=None, out_weights=None,
                      channel_major: bool = False):
-        lon, lat, data, weights = self._prep(lon, lat, data, weights)
+        lon, lat, data, weights, n = self._prep(lon, lat, data, weights)
         shape = (self.n_channels, self.n_targets) if channel_major else \
             (self.n_targets, self.n_channels)
         if out is None:
             out = torch.empty(shape, device=self.device, dtype=torch.float32)
         C.cg_grid_oneshot(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
-                          _ptr(weights), int(lon.numel()), _ptr(out), 1 if channel_major else 0,
+                          _ptr(weights), n, _ptr(out), 1 if channel_major else 0,
                           _ptr(out_weights))
         self._keep = (lon, lat, data, weights)
         return out
+
+    # -- adjoint and kernel-width derivative ------------------------------
+    def degrid(self, ymap, map_weights=None, out=None):
+        """G^T y: the adjoint of the normalised gridding of the last add's
+        samples (ymap [P, C] float32; map_weights = W_p of that gridding, or
+        None for the accumulated weight map).  Returns [N, C] float32."""
+        ymap = torch.as_tensor(ymap, device=self.device, dtype=torch.float32)
+        ymap = ymap.reshape(self.n_targets, self.n_channels).contiguous()
+        if map_weights is not None:
+            map_weights = torch.as_tensor(map_weights, device=self.device,
+                                          dtype=torch.float32).contiguous()
+        n = int(getattr(self, "n_samples", 0))
+        if out is None:
+            out = torch.empty((n, self.n_channels), device=self.device, dtype=torch.float32)
+        C.cg_degrid(self._h, _ptr(ymap), _ptr(map_weights), _ptr(out), n)
+        self._keep_d = (ymap, map_weights)
+        return out
+
+    def dsigma(self, data, grad_out=None, want_dR: bool = True):
+        """d R / d sigma (gauss1d, support fixed; sigma in degrees) for the last
+        add's samples with channel data `data`.  Returns (dR [P, C] or None,
+        sum(grad_out * dR) as a 0-d float64 device tensor or None)."""
+        data = torch.as_tensor(data, device=self.device)
+        if data.dtype not in (torch.float32, torch.bfloat16):
+            data = data.to(torch.float32)
+        data = data.reshape(-1, self.n_channels).contiguous()
+        dR = torch.empty((self.n_targets, self.n_channels), device=self.device,
+                         dtype=torch.float32) if want_dR else None
+        ds = None
+        if grad_out is not None:
+            grad_out = torch.as_tensor(grad_out, device=self.device, dtype=torch.float32)
+            grad_out = grad_out.reshape(self.n_targets, self.n_channels).contiguous()
+            ds = torch.empty((), device=self.device, dtype=torch.float64)
+        C.cg_grid_dsigma(self._h, _ptr(data), self._data_dtype(data), _ptr(grad_out), _ptr(dR),
+                         _ptr(ds))
+        self._keep_s = (data, grad_out)
+        return dR, ds
 
     def reset(self):
         C.cg_grid_reset(self._h)

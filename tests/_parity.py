@@ -50,3 +50,41 @@ def compare_maps(got, got_w, ref, tol=FP32_TOL, wtol=FP32_TOL, channels=None):
     assert me <= tol, "map error %.3e > %.1e" % (me, tol)
     assert mw <= wtol, "weight error %.3e > %.1e" % (mw, wtol)
     return me, mw
+
+
+def _haversine_np(l1, b1, l2, b2):
+    b1, b2 = np.radians(b1), np.radians(b2)
+    dl = np.radians(np.asarray(l2) - l1)
+    h = np.sin(0.5 * (b2 - b1)) ** 2 + np.cos(b1) * np.cos(b2) * np.sin(0.5 * dl) ** 2
+    return 2.0 * np.arcsin(np.sqrt(np.minimum(h, 1.0)))
+
+
+def candidates_near(lon_c, lat_c, lon_s, lat_s, radius_deg, order=None):
+    """Indices of the samples within radius_deg of any centre, as a superset
+    (radius widened by 1e-6 relative): latitude bands from one sort, then the
+    great-circle distance.  Lets the FP64 brute-force oracle evaluate Eq. 1-3
+    exactly for a few targets of a large workload."""
+    lat_s = np.asarray(lat_s)
+    if order is None:
+        order = np.argsort(lat_s, kind="stable")
+    ls = lat_s[order]
+    rad = radius_deg * (1.0 + 1e-6) + 1e-9
+    out = []
+    for lc, bc in zip(np.atleast_1d(lon_c), np.atleast_1d(lat_c)):
+        lo = np.searchsorted(ls, bc - rad, "left")
+        hi = np.searchsorted(ls, bc + rad, "right")
+        idx = order[lo:hi]
+        d = _haversine_np(lc, bc, np.asarray(lon_s)[idx], lat_s[idx])
+        out.append(idx[d <= np.radians(rad)])
+    return np.unique(np.concatenate(out)) if out else np.zeros(0, dtype=np.int64)
+
+
+def oracle_on_targets(wl, tsel, k, data=None, omega="wl"):
+    """oracle.grid_bruteforce restricted to the targets tsel and to the samples
+    that can reach them (exact for those targets)."""
+    data = wl.data if data is None else data
+    om = wl.omega if isinstance(omega, str) else omega
+    cand = candidates_near(wl.lon_t[tsel], wl.lat_t[tsel], wl.lon_s, wl.lat_s, wl.support)
+    return oracle.grid_bruteforce(wl.lon_t[tsel], wl.lat_t[tsel], wl.lon_s[cand], wl.lat_s[cand],
+                                  np.asarray(data, dtype=np.float64)[cand], k,
+                                  None if om is None else np.asarray(om)[cand]), cand

@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the differentiable-workload timings")
     ap.add_argument("--cpu-samples", type=int, default=12000)
     return ap.parse_args()
 
@@ -276,7 +278,8 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
         kbytes = grid_kernel_bytes(wl, dbytes)
         ach = kbytes / (t_grid / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None,
+                "frac": ach / hbm,
+                "traffic": captured_traffic() if args.scale == 1.0 else None,
                 "kernel": "k_grid_tc (tile gridder, BF16 tcgen05 + TMEM)",
                 "bytes_per_launch": kbytes, "peak_source": peaks_src,
                 "tensor_useful_tflops": 2.0 * upd / (t_grid / 1e3) / 1e12,
@@ -296,6 +299,79 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
         "gpu_launches": info1["n_launches"] - info0["n_launches"],
         "clocks": clocks,
     }
+
+
+def time_differentiable(args, dev):
+    """The differentiable workload (2e5 samples x 16 channels -> 256 x 256,
+    sigma = 4', r = 12'): one forward + backward step (one-shot gridding, the
+    adjoint of dL/dR and dL/dsigma) and the 50-step map-making loop, each
+    timed with CUDA events after warm-up."""
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder, mapmaking
+    wl = workloads.diff(scale=1.0)
+    P, C = wl.n_targets, wl.n_channels
+    lon = torch.from_numpy(wl.lon_s).to(dev)
+    lat = torch.from_numpy(wl.lat_s).to(dev)
+    data = torch.from_numpy(wl.data).to(dev)
+    gR = torch.randn((P, C), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=C, device=dev)
+    g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
+    R = torch.empty((P, C), device=dev)
+    W = torch.empty(P, device=dev)
+    gx = torch.empty((wl.n_samples, C), device=dev)
+
+    def step():
+        g.grid_oneshot(lon, lat, data, out=R, out_weights=W)
+        g.degrid(gR, map_weights=W, out=gx)
+        g.dsigma(data, grad_out=gR, want_dR=False)
+
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(5, args.steps)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / steps
+    mapmaking.gd(g, lon, lat, data, steps=50)         # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, losses, _ = mapmaking.gd(g, lon, lat, data, steps=50)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1)
+    g.close()
+    return {"workload": "differentiable: %d samples x %d channels -> %dx%d targets at 2', "
+                        "gauss1d sigma=4', r=12' (fixed in d/dsigma)"
+                        % (wl.n_samples, C, wl.grid_shape[1], wl.grid_shape[0]),
+            "ms_forward_backward": ms_step,
+            "ms_mapmaking_50_steps": ms_loop,
+            "mapmaking_loss_first_last": [float(losses[0]), float(losses[-1])]}
+
+
+# DRAM bytes (read + write) of one k_grid_tc launch on the full cube, from an
+# ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (summary under
+# profiles/); valid only for the kernel source it was taken with.
+TRAFFIC_CAPTURE = {"source": "paper_1604_06667_gb300/csrc/k_grid_tc.cu",
+                   "sha256": "c0e431261b9d124009d2fea838e181e19bd6f1e2825e487fb4dd08991f36c970",
+                   "bytes_per_launch": 864511232 + 274457088}
+
+
+def captured_traffic():
+    import hashlib
+    if not TRAFFIC_CAPTURE["sha256"]:
+        return None
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_launch"] if sha == TRAFFIC_CAPTURE["sha256"] else None
 
 
 def grid_kernel_bytes(wl, dbytes):
@@ -365,6 +441,9 @@ def main():
     }
     if len(results) == 2:
         line["mixed_over_fp32"] = results["bf16"]["value"] / results["fp32"]["value"]
+    if not args.no_extra and args.scale == 1.0:
+        progress("differentiable workload")
+        line["differentiable"] = time_differentiable(args, dev)
 
     # ---- end to end: pinned host inputs, copies inside the timed region ----
     if not args.no_e2e:

@@ -209,6 +209,14 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
 cg_status cg_unit_vectors(const double* lon_deg, const double* lat_deg, int64_t n, double* xyz,
                           void* stream);
 
+/* Register-blocking shape of the FP32 CUDA-core gridder (a tuning knob; the
+ * result differs only in the rounding of the weight sums): -1 = by channel
+ * count (default), 0 .. CG_F32_SHAPES-1 = (targets x channels per thread,
+ * channel groups) of <1,4,1> <1,8,1> <1,8,2> <2,8,4> <2,16,4> <4,16,8>
+ * <4,16,16>.  The batch autotuner picks it per job. */
+#define CG_F32_SHAPES 7
+cg_status cg_set_f32_shape(cg_grid* g, int32_t shape);
+
 /* Adjoint of the normalised gridding operator (paper Eq. 1-3 read as a
  * linear map R = G D with G[p][n] = omega_n w_pn / W_p): degridding,
  *   out[n][c] = sum_p G[p][n] map[p][c],
@@ -283,6 +291,64 @@ cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
 #define CG_NOALLOC_MAX_SAMPLES 262144
 cg_status cg_sort_samples_noalloc(int32_t nside, const double* lon_deg, const double* lat_deg,
                                   int64_t n, int64_t* sorted_pix, int64_t* perm, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent gridding jobs replayed as one CUDA graph.
+ *
+ * The paper grids one survey at a time; a batch runs many jobs of uneven
+ * sample count, channel count, target grid and kernel width together.  Each
+ * job has its own handle (targets, kernel and channel count set by the
+ * caller with cg_grid_create / cg_set_kernel) and its own caller-owned
+ * device arrays; a job computes exactly what cg_grid_oneshot computes.
+ * ------------------------------------------------------------------------ */
+typedef struct cg_job {
+  cg_grid* grid;                  /* the job's handle (one handle per job)    */
+  const double* lon_deg;          /* device [n_samples] float64               */
+  const double* lat_deg;          /* device [n_samples] float64               */
+  const void* data;               /* device [n_samples][C], data_dtype        */
+  int32_t data_dtype;             /* CG_F32 or CG_BF16                        */
+  const float* weights;           /* device [n_samples] float32 or NULL       */
+  int64_t n_samples;              /* >= 1                                     */
+  float* out;                     /* device float32 map (layout as below)     */
+  int32_t layout_channel_major;   /* 0: [n_targets][C], 1: [C][n_targets]     */
+  float* out_weights;             /* device float32 [n_targets] or NULL       */
+} cg_job;
+
+typedef struct cg_batch cg_batch;
+
+/* Plan a batch: copies the job descriptors (the arrays they point to must
+ * stay valid while the batch is used) and assigns the jobs to n_streams
+ * parallel branches (1 .. 64), largest estimated cost first onto the least
+ * loaded branch.  CG_EINVAL for a job without a kernel, with no samples or a
+ * null pointer, or whose handle another job also uses. */
+cg_status cg_batch_create(cg_batch** out, const cg_job* jobs, int32_t n_jobs, int32_t n_streams);
+
+/* Autotune (synchronising): for every job, time `reps` one-shot runs of each
+ * candidate -- the FP32 gridder's register-blocking shapes next to the
+ * default for its channel count, and (allow_tc != 0, BF16 data, C % 8 == 0)
+ * the tensor-core form -- and keep the fastest.  Invalidates a captured graph. */
+cg_status cg_batch_autotune(cg_batch* b, int32_t reps, int32_t allow_tc);
+
+/* Run every job once eagerly (so that workspaces reach their final size),
+ * then capture all jobs into one CUDA graph on `stream` (NULL: a private
+ * stream): a fork, each job's one-shot pipeline on its branch, a join. */
+cg_status cg_batch_capture(cg_batch* b, void* stream);
+
+/* Replay the captured graph on `stream` (one launch; asynchronous).
+ * CG_ESTATE before cg_batch_capture.  Device errors of a job are reported
+ * by cg_sync on that job's handle. */
+cg_status cg_batch_run(cg_batch* b, void* stream);
+
+/* The planner's and autotuner's choice for one job: path (CG_PATH_*), FP32
+ * shape index (-1: default), tuned ms per one-shot run, branch index. */
+cg_status cg_batch_get_choice(cg_batch* b, int32_t job, int32_t* path, int32_t* f32_shape,
+                              double* ms, int32_t* stream_index);
+
+/* Kernels recorded in the captured graph and the number of branches. */
+cg_status cg_batch_info(cg_batch* b, int64_t* graph_kernels, int32_t* n_streams);
+
+/* Release the graph, branch streams and events (not the jobs' handles). */
+cg_status cg_batch_destroy(cg_batch* b);
 
 #ifdef __cplusplus
 }

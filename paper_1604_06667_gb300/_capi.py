@@ -32,6 +32,15 @@ CG_N_STAGES = 5
 STAGE_NAMES = ("keys", "sort", "index", "grid", "finalize")
 
 
+class CgJob(ctypes.Structure):
+    """cg_job of include/cygrid_gb300.h."""
+    _fields_ = [("grid", ctypes.c_void_p), ("lon_deg", ctypes.c_void_p),
+                ("lat_deg", ctypes.c_void_p), ("data", ctypes.c_void_p),
+                ("data_dtype", ctypes.c_int32), ("weights", ctypes.c_void_p),
+                ("n_samples", ctypes.c_int64), ("out", ctypes.c_void_p),
+                ("layout_channel_major", ctypes.c_int32), ("out_weights", ctypes.c_void_p)]
+
+
 class CygridError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
@@ -58,12 +67,21 @@ SIGNATURES = {
     "cg_get_info": [_vp, ctypes.POINTER(CgInfo)],
     "cg_ang2pix_ring": [_i32, _vp, _vp, _i64, _vp, _vp],
     "cg_unit_vectors": [_vp, _vp, _i64, _vp, _vp],
+    "cg_set_f32_shape": [_vp, _i32],
     "cg_degrid": [_vp, _vp, _vp, _vp, _i64],
     "cg_grid_dsigma": [_vp, _vp, _i32, _vp, _vp, _vp],
     "cg_grid_export_index": [_vp, _vp, _vp, _vp, _i64],
     "cg_set_timing": [_vp, _i32],
     "cg_read_timing": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)],
     "cg_sort_samples_noalloc": [_i32, _vp, _vp, _i64, _vp, _vp, _vp],
+    "cg_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(CgJob), _i32, _i32],
+    "cg_batch_autotune": [_vp, _i32, _i32],
+    "cg_batch_capture": [_vp, _vp],
+    "cg_batch_run": [_vp, _vp],
+    "cg_batch_get_choice": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                            ctypes.POINTER(_dbl), ctypes.POINTER(_i32)],
+    "cg_batch_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
+    "cg_batch_destroy": [_vp],
 }
 
 CG_NOALLOC_MAX_SAMPLES = 262144
@@ -117,12 +135,20 @@ cg_sync = _call("cg_sync")
 cg_get_info = _call("cg_get_info")
 cg_ang2pix_ring = _call("cg_ang2pix_ring")
 cg_unit_vectors = _call("cg_unit_vectors")
+cg_set_f32_shape = _call("cg_set_f32_shape")
 cg_degrid = _call("cg_degrid")
 cg_grid_dsigma = _call("cg_grid_dsigma")
 cg_grid_export_index = _call("cg_grid_export_index")
 cg_set_timing = _call("cg_set_timing")
 cg_read_timing = _call("cg_read_timing")
 cg_sort_samples_noalloc = _call("cg_sort_samples_noalloc")
+cg_batch_create = _call("cg_batch_create")
+cg_batch_autotune = _call("cg_batch_autotune")
+cg_batch_capture = _call("cg_batch_capture")
+cg_batch_run = _call("cg_batch_run")
+cg_batch_get_choice = _call("cg_batch_get_choice")
+cg_batch_info = _call("cg_batch_info")
+cg_batch_destroy = _call("cg_batch_destroy")
 
 
 def cg_last_error() -> str:

@@ -141,14 +141,21 @@ void free_all(cg_grid* g) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// Reset: the first add after it stores instead of accumulating (both
+// gridders write every valid slot of every tile), so the accumulators are
+// only cleared when a finalize finds no add since the reset.
 cg_status zero_acc(cg_grid* g) {
-  const int64_t slots = g->n_slots;
-  CG_CUDA(cudaMemsetAsync(g->acc_num, 0, sizeof(float) * (size_t)slots * g->C, g->stream),
-          "reset");
-  CG_CUDA(cudaMemsetAsync(g->acc_w, 0, sizeof(float2) * (size_t)slots, g->stream), "reset");
   CG_CUDA(cudaMemsetAsync(g->d_pairs, 0, sizeof(unsigned long long), g->stream), "reset");
   g->acc_empty = true;
   g->total_n = 0;
+  return CG_OK;
+}
+
+cg_status clear_if_empty(cg_grid* g, const char* where) {
+  if (!g->acc_empty) return CG_OK;
+  const int64_t slots = g->n_slots;
+  CG_CUDA(cudaMemsetAsync(g->acc_num, 0, sizeof(float) * (size_t)slots * g->C, g->stream), where);
+  CG_CUDA(cudaMemsetAsync(g->acc_w, 0, sizeof(float2) * (size_t)slots, g->stream), where);
   return CG_OK;
 }
 
@@ -227,6 +234,17 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
 }
 
 }  // namespace
+
+// error reporting for the other host translation units (the batch API)
+cg_status cg::batch_fail(cg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
 
 extern "C" {
 
@@ -355,6 +373,8 @@ cg_status cg_grid_finalize(cg_grid* g, float* out, int32_t layout_channel_major,
   if (!g) return fail(CG_EINVAL, "cg_grid_finalize: null handle");
   if (!out) return fail(CG_EINVAL, "cg_grid_finalize: out is null");
   CG_CUDA(cudaSetDevice(g->device), "cg_grid_finalize");
+  cg_status st = clear_if_empty(g, "cg_grid_finalize");
+  if (st != CG_OK) return st;
   cudaEvent_t t0 = tmark(g);
   CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_finalize");
   tstage(g, 4, t0, tmark(g));
@@ -377,6 +397,8 @@ cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_d
               layout_channel_major ? nullptr : out, out_weights, &fused);
   if (st != CG_OK) return st;
   if (fused) return CG_OK;  // the tensor-core epilogue already wrote Eq. 3
+  st = clear_if_empty(g, "cg_grid_oneshot");
+  if (st != CG_OK) return st;
   cudaEvent_t t0 = tmark(g);
   CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_oneshot");
   tstage(g, 4, t0, tmark(g));
@@ -482,6 +504,15 @@ cg_status cg_ang2pix_ring(int32_t nside, const double* lon_deg, const double* la
     return fail(CG_EINVAL, "cg_ang2pix_ring: null pointer");
   CG_CUDA(ang2pix_export(nside, lon_deg, lat_deg, n, pix, static_cast<cudaStream_t>(stream)),
           "cg_ang2pix_ring");
+  return CG_OK;
+}
+
+cg_status cg_set_f32_shape(cg_grid* g, int32_t shape) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_set_f32_shape: null handle");
+  if (shape < -1 || shape >= kF32Configs)
+    return fail(CG_EINVAL, "cg_set_f32_shape: shape must be -1 or in [0, %d)", kF32Configs);
+  g->f32_cfg = shape;
   return CG_OK;
 }
 

@@ -76,6 +76,7 @@ struct cg_grid {
   int64_t P = 0;
   int32_t C = 0;
   int32_t path = CG_PATH_AUTO;
+  int32_t f32_cfg = -1;           // FP32 gridder shape (-1: by channel count)
   int32_t last_path = CG_PATH_FP32;
 
   // targets, in tile order (slot = tile * T + lane; empty slots marked)
@@ -195,6 +196,9 @@ cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t
 
 // k_grid.cu -- the tile gridder (FP32 CUDA-core form).
 cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype);
+constexpr int kF32Configs = 7;
+cg_status batch_fail(cg_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));      // register-blocking shapes of the FP32 gridder
+int f32_default_config(int C);
 // the same into given accumulators; dscale != 0 evaluates w d^2 dscale
 // instead of w (the d/dsigma pass) and counts no pairs
 cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,

@@ -389,16 +389,33 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
   // only the handle's own accumulation counts pairs (not the scratch passes)
   a.pairs = (dscale != 0.f || acc_num != g->acc_num) ? nullptr : g->d_pairs;
   g->n_launches += 1;
-  const int C = g->C;
   const int64_t nt = g->t64.n_tiles;
   cudaStream_t s = g->stream;
-  if (C <= 4) return launch<1, 4, 1>(a, nt, dtype, s);
-  if (C <= 8) return launch<1, 8, 1>(a, nt, dtype, s);
-  if (C <= 16) return launch<1, 8, 2>(a, nt, dtype, s);
-  if (C <= 32) return launch<2, 8, 4>(a, nt, dtype, s);
-  if (C <= 64) return launch<2, 16, 4>(a, nt, dtype, s);
-  if (C <= 128) return launch<4, 16, 8>(a, nt, dtype, s);
-  return launch<4, 16, 16>(a, nt, dtype, s);
+  int cfg = g->f32_cfg;
+  if (cfg < 0 || cfg >= kF32Configs) cfg = f32_default_config(g->C);
+  switch (cfg) {
+    case 0: return launch<1, 4, 1>(a, nt, dtype, s);
+    case 1: return launch<1, 8, 1>(a, nt, dtype, s);
+    case 2: return launch<1, 8, 2>(a, nt, dtype, s);
+    case 3: return launch<2, 8, 4>(a, nt, dtype, s);
+    case 4: return launch<2, 16, 4>(a, nt, dtype, s);
+    case 5: return launch<4, 16, 8>(a, nt, dtype, s);
+    default: return launch<4, 16, 16>(a, nt, dtype, s);
+  }
+}
+
+// Register-blocking shapes of the FP32 gridder, (targets x channels per
+// thread in phase B, channel groups): 0 <1,4,1> 1 <1,8,1> 2 <1,8,2>
+// 3 <2,8,4> 4 <2,16,4> 5 <4,16,8> 6 <4,16,16>; a CTA covers CB * NCG channels
+// of its tile, more channels take more CTAs.  The default follows C.
+int f32_default_config(int C) {
+  if (C <= 4) return 0;
+  if (C <= 8) return 1;
+  if (C <= 16) return 2;
+  if (C <= 32) return 3;
+  if (C <= 64) return 4;
+  if (C <= 128) return 5;
+  return 6;
 }
 
 }  // namespace cg

@@ -63,6 +63,10 @@ class Gridder:
         C.cg_set_path(self._h, int(path))
         return self
 
+    def set_f32_shape(self, shape: int):
+        C.cg_set_f32_shape(self._h, int(shape))
+        return self
+
     # -- gridding -------------------------------------------------------
     @staticmethod
     def _data_dtype(data):

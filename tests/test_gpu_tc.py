@@ -164,3 +164,56 @@ def test_tc_rejects_unsupported_inputs():
         g.grid(wl.lon_s, wl.lat_s, torch.from_numpy(wl.data))    # FP32 data, C % 8 != 0
     assert ei.value.status == _capi.CG_EINVAL
     g.close()
+
+
+def _destination(lon1, lat1, d, beta):
+    """Point at great-circle distance d (rad) and bearing beta (rad) from
+    (lon1, lat1) in degrees (spherical direct problem, FP64)."""
+    b1, l1 = np.radians(lat1), np.radians(lon1)
+    b2 = np.arcsin(np.sin(b1) * np.cos(d) + np.cos(b1) * np.sin(d) * np.cos(beta))
+    l2 = l1 + np.arctan2(np.sin(beta) * np.sin(d) * np.cos(b1),
+                         np.cos(d) - np.sin(b1) * np.sin(b2))
+    return np.degrees(l2), np.degrees(b2)
+
+
+@pytest.mark.parametrize("path", ["fp32", "tc"])
+def test_cut_edges_exact(path):
+    """Samples placed at d = r (1 + delta) around targets, delta from 1e-8 to
+    1e-5 on both sides (chord^2 within and at the edges of the +-1e-5 guard
+    band): the pair count equals the FP64 oracle's exactly, on both forms."""
+    import torch
+    from paper_1604_06667_gb300 import Gridder, _capi
+    ARC = 1.0 / 60.0
+    sigma = 3.0 * ARC
+    r = 3.0 * sigma
+    lon_t, lat_t = workloads.car_grid(140.0, -35.0, 12, 12, sigma / 2.0)
+    rng = np.random.Generator(np.random.PCG64(606))
+    deltas = np.array([1e-8, 1e-7, 1e-6, 4.9e-6, 4.98e-6, 5.0e-6, 5.02e-6, 5.1e-6, 1e-5])
+    deltas = np.concatenate([deltas, -deltas])
+    centre = np.nonzero((np.abs(np.arange(144) // 12 - 5.5) < 3) & (np.abs(np.arange(144) % 12 - 5.5) < 3))[0]
+    lon_s, lat_s = [], []
+    for p in centre:
+        for dl in deltas:
+            beta = rng.uniform(0, 2 * np.pi, 3)
+            lo, la = _destination(lon_t[p], lat_t[p], np.radians(r) * (1.0 + dl), beta)
+            lon_s.append(lo)
+            lat_s.append(la)
+    lon_s, lat_s = np.concatenate(lon_s), np.concatenate(lat_s)
+    data = rng.normal(0, 1, (lon_s.size, 16)).astype(np.float32)
+    k = oracle.gauss1d(sigma, r)
+    g = Gridder(lon_t, lat_t, n_channels=16)
+    g.set_kernel("gauss1d", (sigma,), r, sigma / 2.0)
+    g.set_path(_capi.CG_PATH_TC if path == "tc" else _capi.CG_PATH_FP32)
+    d = torch.from_numpy(data)
+    if path == "tc":
+        d = d.to(torch.bfloat16)
+    w = torch.empty(lon_t.size, device="cuda")
+    g.grid_oneshot(lon_s, lat_s, d, out_weights=w)
+    g.sync()
+    npairs = g.info()["n_pairs"]
+    g.close()
+    ref = oracle.grid_bruteforce(lon_t, lat_t, lon_s, lat_s, d.float().numpy(), k)
+    assert npairs == ref.npairs
+    on = ref.wsum > 0
+    assert np.array_equal(on, w.cpu().numpy() > 0)
+    assert np.max(np.abs(w.cpu().numpy()[on] - ref.wsum[on]) / ref.wsum[on]) < 5e-5

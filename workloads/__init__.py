@@ -243,3 +243,86 @@ def random_field(cid: int, n: int, n_targets_side: int, C: int, lon0: float, lat
     return Workload("random", lon, lat, data, om, lon_t, lat_t,
                     {"type": "gauss1d", "sigma": sigma_deg}, 3.0 * sigma_deg,
                     sigma_deg / 2.0, (n_targets_side, n_targets_side), {})
+
+
+# ---------------------------------------------------------------------------
+# Batched jobs (many independent gridding problems of uneven size)
+# ---------------------------------------------------------------------------
+BATCH_CHANNELS = (1, 16, 64, 512)
+BATCH_SIDES = (64, 128, 256, 512, 1024)
+
+
+def batch_specs(n_jobs: int = 64, seed: int | None = None, n_range=(1e4, 1e6),
+                channels=BATCH_CHANNELS, sides=BATCH_SIDES) -> list:
+    """Job descriptions: sample count log-uniform in n_range, channels and
+    target-grid side drawn from the given sets, sigma ~ U[1', 8'], pixel =
+    sigma / 2, support 3 sigma, field centre lon ~ U[0, 360), lat ~ U[-60, 60]
+    (moved towards the equator when the field would reach |lat| > 88), data
+    dtype alternating FP32 / BF16."""
+    rng = rng_for(4, seed)
+    specs = []
+    for j in range(n_jobs):
+        n = int(round(10.0 ** rng.uniform(math.log10(n_range[0]), math.log10(n_range[1]))))
+        C = int(rng.choice(channels))
+        side = int(rng.choice(sides))
+        sigma = rng.uniform(1.0, 8.0) * ARCMIN
+        step = sigma / 2.0
+        half = 0.5 * side * step
+        lon0 = rng.uniform(0.0, 360.0)
+        lat0 = float(np.clip(rng.uniform(-60.0, 60.0), -88.0 + half, 88.0 - half)) \
+            if half < 88.0 else 0.0
+        specs.append({"job": j, "n": n, "C": C, "side": side, "sigma": sigma, "step": step,
+                      "lon0": lon0, "lat0": lat0, "dtype": "bf16" if j % 2 else "f32",
+                      "seed": int(rng.integers(0, 2 ** 31))})
+    return specs
+
+
+def batch_job(spec: dict) -> Workload:
+    """A job of batch_specs as a numpy workload: samples uniform in the field,
+    data N(0, 1) plus three Gaussian sources (FWHM 4 sigma) with per-channel
+    amplitudes U[1, 10]."""
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    n, C, side, step = spec["n"], spec["C"], spec["side"], spec["step"]
+    half = 0.5 * side * step
+    lon = spec["lon0"] + rng.uniform(-half, half, n)
+    lat = spec["lat0"] + rng.uniform(-half, half, n)
+    data = rng.standard_normal((n, C), dtype=np.float32)
+    fwhm = 4.0 * spec["sigma"]
+    for _ in range(3):
+        lk = spec["lon0"] + rng.uniform(-half, half)
+        bk = spec["lat0"] + rng.uniform(-half, half)
+        prof = _flat_gauss(lon, lat, lk, bk, fwhm).astype(np.float32)
+        data += prof[:, None] * rng.uniform(1.0, 10.0, C).astype(np.float32)[None, :]
+    lon_t, lat_t = car_grid(spec["lon0"], spec["lat0"], side, side, step)
+    return Workload("batch%d" % spec["job"], lon, lat, data, None, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": spec["sigma"]}, 3.0 * spec["sigma"],
+                    spec["sigma"] / 2.0, (side, side), dict(spec))
+
+
+def batch_job_device(spec: dict, device, dtype_override=None):
+    """batch_job with the channel data generated on the device (seeded torch
+    generator; used by the benchmark, where numpy would spend tens of seconds
+    on the 3e9 values of a 64-job batch).  Returns (lon_s, lat_s, data[n, C]
+    float32 on the device, lon_t, lat_t, spec)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    n, C, side, step = spec["n"], spec["C"], spec["side"], spec["step"]
+    half = 0.5 * side * step
+    lon = spec["lon0"] + rng.uniform(-half, half, n)
+    lat = spec["lat0"] + rng.uniform(-half, half, n)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(spec["seed"])
+    data = torch.randn((n, C), generator=gen, device=device, dtype=torch.float32)
+    fwhm = 4.0 * spec["sigma"]
+    lon_d = torch.from_numpy(lon).to(device)
+    lat_d = torch.from_numpy(lat).to(device)
+    for _ in range(3):
+        lk = spec["lon0"] + rng.uniform(-half, half)
+        bk = spec["lat0"] + rng.uniform(-half, half)
+        dx = (lon_d - lk) * math.cos(math.radians(bk))
+        dy = lat_d - bk
+        prof = torch.exp(-(dx * dx + dy * dy) / (2.0 * fwhm * fwhm)).float()
+        amp = torch.from_numpy(rng.uniform(1.0, 10.0, C).astype(np.float32)).to(device)
+        data += prof[:, None] * amp[None, :]
+    lon_t, lat_t = car_grid(spec["lon0"], spec["lat0"], side, side, step)
+    return lon, lat, data, lon_t, lat_t

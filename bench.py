@@ -428,6 +428,42 @@ def time_batched(args, dev, n_jobs=64):
     return res
 
 
+def time_example1(args, dev):
+    """The paper's Example 1 (Sect. 4) at 1e8 samples: 5 x 5 deg field, 200"
+    pixels, FWHM 300" Gaussian, one channel of noise -- the paper quotes about
+    67 s on 16 cores for this size.  One-shot calls timed with CUDA events."""
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder
+    lon, lat, data, lon_t, lat_t, kern, support, maxres = workloads.example1_device(dev)
+    g = Gridder(lon_t, lat_t, n_channels=1, device=dev)
+    g.set_kernel("gauss1d", (kern["sigma"],), support, maxres)
+    out = torch.empty((g.n_targets, 1), device=dev)
+    w = torch.empty(g.n_targets, device=dev)
+    for _ in range(2):
+        g.grid_oneshot(lon, lat, data, out=out, out_weights=w)
+    g.sync()
+    g.set_timing(True)
+    g.read_timing()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 3
+    e0.record(stream)
+    for _ in range(steps):
+        g.grid_oneshot(lon, lat, data, out=out, out_weights=w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stages = g.read_timing()
+    info = g.info()
+    g.close()
+    return {"workload": "paper Example 1: %d samples uniform in 5x5 deg, 90x90 targets at 200\", "
+                        "FWHM 300\" Gaussian, support 3 sigma, one channel" % lon.numel(),
+            "ms_per_call": ms, "pairs_per_call": info["n_pairs"],
+            "stages_ms": {k: v / steps for k, v in stages.items() if k != "grid_launches"},
+            "paper_16_cores_s": 67.0, "speedup_vs_paper_16_cores": 67.0e3 / ms}
+
+
 def grid_kernel_bytes(wl, dbytes):
     """Algorithmic bytes of one gridder launch: every sample's channel row and
     its sorted 32-byte position record read once, the map and weight map
@@ -500,6 +536,8 @@ def main():
         line["differentiable"] = time_differentiable(args, dev)
         progress("batched workload")
         line["batched"] = time_batched(args, dev)
+        progress("paper example 1")
+        line["paper_example1"] = time_example1(args, dev)
 
     # ---- end to end: pinned host inputs, copies inside the timed region ----
     if not args.no_e2e:

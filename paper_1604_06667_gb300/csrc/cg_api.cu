@@ -130,6 +130,8 @@ void free_all(cg_grid* g) {
   dfree(g->ds_num0, s);
   dfree(g->ds_w0, s);
   dfree(g->ds_part, s);
+  dfree(g->part_num, s);
+  dfree(g->part_w, s);
   dfree(g->acc_num, s);
   dfree(g->acc_w, s);
   dfree(g->d_err, s);

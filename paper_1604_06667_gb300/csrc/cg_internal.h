@@ -136,6 +136,11 @@ struct cg_grid {
   float2* ds_w0 = nullptr;        // [slots]
   double* ds_part = nullptr;      // per-block partial sums
 
+  // candidate-split partial sums of the FP32 gridder
+  float* part_num = nullptr;      // [n_split][slots][C]
+  float2* part_w = nullptr;       // [n_split][slots]
+  size_t part_cap_num = 0, part_cap_w = 0;
+
   // accumulators (tile order)
   float* acc_num = nullptr;       // [slots][C]
   float2* acc_w = nullptr;        // [slots] double-float weight sum

@@ -49,6 +49,13 @@ struct GridArgs {
   float2* acc_w;
   int accumulate;
   unsigned long long* pairs;
+  // candidate splits (blockIdx.z): a tile's candidates are shared by n_split
+  // CTAs that write partial sums, summed by k_split_reduce in split order
+  const int32_t* tile_cand;
+  int n_split;
+  int64_t n_slots;
+  float* part_num;      // [n_split][slots][C]
+  float2* part_w;       // [n_split][slots]
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -144,8 +151,17 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   const DT* data = static_cast<const DT*>(a.data);
   const int C = a.C;
   const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
+  // this CTA's share [c_lo, c_hi) of the tile's candidates (whole chunks)
+  int c_lo = 0, c_hi = 0x7fffffff;
+  if (a.n_split > 1) {
+    const int total_t = a.tile_cand[tile];
+    const int per = ((total_t + a.n_split - 1) / a.n_split + K - 1) / K * K;
+    c_lo = (int)blockIdx.z * per;
+    c_hi = min(total_t, c_lo + per);
+  }
+  int cbase = 0;   // the tile's candidates before the current range batch
 
-  for (int64_t rb = r0; rb < r1; rb += kRangeBatch) {
+  for (int64_t rb = r0; rb < r1 && cbase < c_hi; rb += kRangeBatch) {
     const int nr = (int)((r1 - rb) < kRangeBatch ? (r1 - rb) : kRangeBatch);
     __syncthreads();
     if (tid < 32) {
@@ -172,12 +188,15 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     }
     __syncthreads();
     const int total = rg_pre[nr];
+    const int v_lo = max(0, min(total, c_lo - cbase));
+    const int v_hi = max(0, min(total, c_hi - cbase));
+    cbase += total;
 
-    for (int v0 = 0; v0 < total; v0 += K) {
+    for (int v0 = v_lo; v0 < v_hi; v0 += K) {
       // ---- stage candidates ----
       if (tid < K) {
         const int v = v0 + tid;
-        if (v < total) {
+        if (v < v_hi) {
           int lo = 0, hi = nr - 1;  // last range with rg_pre <= v
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -301,17 +320,20 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   }
 
   // ---- epilogue: numerator ----
+  const bool split = a.n_split > 1;
 #pragma unroll
   for (int i = 0; i < PB; ++i) {
     const int64_t sl = tile * kTile + pg * PB + i;
     if (a.tgt_perm[sl] == 0xffffffffu) continue;
-    float* dst = a.acc_num + (size_t)sl * C;
+    float* dst = split ? a.part_num + ((size_t)blockIdx.z * a.n_slots + sl) * C
+                       : a.acc_num + (size_t)sl * C;
+    const bool add = a.accumulate && !split;
 #pragma unroll
     for (int q = 0; q < CB / 4; ++q)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = c_base + 4 * cg + 4 * NCG * q + j;
-        if (c < C) dst[c] = a.accumulate ? dst[c] + acc[i][4 * q + j] : acc[i][4 * q + j];
+        if (c < C) dst[c] = add ? dst[c] + acc[i][4 * q + j] : acc[i][4 * q + j];
       }
   }
   // ---- epilogue: weight map and pair count (first channel slab only) ----
@@ -334,6 +356,10 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
       c += (s - (t - bp2)) + (v.x - bp2) + v.y;
       s = t;
     }
+    if (split) {
+      a.part_w[(size_t)blockIdx.z * a.n_slots + slot] = make_float2(s, c);
+      return;
+    }
     float2 old = a.accumulate ? a.acc_w[slot] : make_float2(0.f, 0.f);
     const float t = old.x + s;
     const float bp2 = t - old.x;
@@ -342,16 +368,105 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   }
 }
 
+// Sum the candidate-split partials in split order into the accumulators.
+__global__ void k_split_reduce(const float* __restrict__ part_num,
+                               const float2* __restrict__ part_w,
+                               const uint32_t* __restrict__ perm, int64_t n_slots, int C,
+                               int n_split, int accumulate, float* __restrict__ acc_num,
+                               float2* __restrict__ acc_w) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_slots * (C + 1)) return;
+  if (e < n_slots * C) {
+    const int64_t sl = e / C;
+    if (perm[sl] == 0xffffffffu) return;
+    float v = 0.f;
+    for (int z = 0; z < n_split; ++z) v += part_num[(size_t)z * n_slots * C + e];
+    acc_num[e] = accumulate ? acc_num[e] + v : v;
+    return;
+  }
+  const int64_t sl = e - n_slots * C;
+  if (perm[sl] == 0xffffffffu) return;
+  float s = 0.f, c = 0.f;
+  for (int z = 0; z < n_split; ++z) {
+    const float2 v = part_w[(size_t)z * n_slots + sl];
+    const float t = s + v.x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v.x - bp) + v.y;
+    s = t;
+  }
+  float2 old = accumulate ? acc_w[sl] : make_float2(0.f, 0.f);
+  const float t = old.x + s;
+  const float bp = t - old.x;
+  const float err = (old.x - (t - bp)) + (s - bp);
+  acc_w[sl] = make_float2(t, old.y + c + err);
+}
+
+// Candidate splits for a launch: enough CTAs to fill the GPU when the
+// targets form few tiles (e.g. 8,100 targets and 1e8 samples).
+template <int PB, int CB, int NCG>
+int splits_for(int64_t n_tiles, int C, int n_sms) {
+  constexpr int NTH = (kTile / PB) * NCG;
+  constexpr int CPAD = CB * NCG;
+  const int64_t ctas = n_tiles * ((C + CPAD - 1) / CPAD);
+  const int64_t want = (int64_t)n_sms * 1024;   // threads to fill the SMs
+  int64_t s = (want + ctas * NTH - 1) / (ctas * NTH);
+  if (s < 1) s = 1;
+  if (s > 64) s = 64;
+  return (int)s;
+}
+
 template <int PB, int CB, int NCG>
 cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s) {
   constexpr int NTH = (kTile / PB) * NCG;
   constexpr int CPAD = CB * NCG;
-  const dim3 grid((unsigned)n_tiles, (unsigned)((a.C + CPAD - 1) / CPAD));
+  const dim3 grid((unsigned)n_tiles, (unsigned)((a.C + CPAD - 1) / CPAD), (unsigned)a.n_split);
   if (n_tiles == 0) return cudaSuccess;
   if (dtype == CG_BF16)
     k_grid_f32<PB, CB, NCG, __nv_bfloat16><<<grid, NTH, 0, s>>>(a);
   else
     k_grid_f32<PB, CB, NCG, float><<<grid, NTH, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// One FP32 gridder pass: choose the candidate splits, grow the partial-sum
+// scratch if needed, launch, and reduce the splits.
+template <int PB, int CB, int NCG>
+cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
+  const int64_t nt = g->t64.n_tiles;
+  cudaStream_t s = g->stream;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  a.n_split = splits_for<PB, CB, NCG>(nt, a.C, nsm);
+  a.part_num = nullptr;
+  a.part_w = nullptr;
+  if (a.n_split > 1) {
+    const size_t need_n = (size_t)a.n_split * (size_t)g->n_slots * (size_t)a.C;
+    const size_t need_w = (size_t)a.n_split * (size_t)g->n_slots;
+    cudaError_t e;
+    if (g->part_cap_num < need_n) {
+      dfree(g->part_num, s);
+      g->part_cap_num = 0;
+      if ((e = dalloc(&g->part_num, need_n, s)) != cudaSuccess) return e;
+      g->part_cap_num = need_n;
+    }
+    if (g->part_cap_w < need_w) {
+      dfree(g->part_w, s);
+      g->part_cap_w = 0;
+      if ((e = dalloc(&g->part_w, need_w, s)) != cudaSuccess) return e;
+      g->part_cap_w = need_w;
+    }
+    a.part_num = g->part_num;
+    a.part_w = g->part_w;
+  }
+  g->n_launches += 1;
+  cudaError_t e = launch<PB, CB, NCG>(a, nt, dtype, s);
+  if (e != cudaSuccess || a.n_split <= 1 || nt == 0) return e;
+  const int64_t m = g->n_slots * (int64_t)(a.C + 1);
+  k_split_reduce<<<ceil_div(m, 256), 256, 0, s>>>(a.part_num, a.part_w, a.tgt_perm, g->n_slots,
+                                                  a.C, a.n_split, a.accumulate, a.acc_num,
+                                                  a.acc_w);
+  g->n_launches += 1;
   return cudaGetLastError();
 }
 
@@ -388,19 +503,18 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
   a.accumulate = accumulate;
   // only the handle's own accumulation counts pairs (not the scratch passes)
   a.pairs = (dscale != 0.f || acc_num != g->acc_num) ? nullptr : g->d_pairs;
-  g->n_launches += 1;
-  const int64_t nt = g->t64.n_tiles;
-  cudaStream_t s = g->stream;
+  a.tile_cand = g->t64.tile_cand;
+  a.n_slots = g->n_slots;
   int cfg = g->f32_cfg;
   if (cfg < 0 || cfg >= kF32Configs) cfg = f32_default_config(g->C);
   switch (cfg) {
-    case 0: return launch<1, 4, 1>(a, nt, dtype, s);
-    case 1: return launch<1, 8, 1>(a, nt, dtype, s);
-    case 2: return launch<1, 8, 2>(a, nt, dtype, s);
-    case 3: return launch<2, 8, 4>(a, nt, dtype, s);
-    case 4: return launch<2, 16, 4>(a, nt, dtype, s);
-    case 5: return launch<4, 16, 8>(a, nt, dtype, s);
-    default: return launch<4, 16, 16>(a, nt, dtype, s);
+    case 0: return run<1, 4, 1>(g, a, dtype);
+    case 1: return run<1, 8, 1>(g, a, dtype);
+    case 2: return run<1, 8, 2>(g, a, dtype);
+    case 3: return run<2, 8, 4>(g, a, dtype);
+    case 4: return run<2, 16, 4>(g, a, dtype);
+    case 5: return run<4, 16, 8>(g, a, dtype);
+    default: return run<4, 16, 16>(g, a, dtype);
   }
 }
 

@@ -145,3 +145,35 @@ def test_diff_full_forward_adjoint_dsigma_mapmaking():
     assert alpha > 0
     assert np.all(np.diff(losses) <= 1e-6 * losses[0])
     assert losses[-1] < losses[0]
+
+
+def _host_wl(lon, lat, data, lon_t, lat_t, kern, support):
+    class W:
+        pass
+    wl = W()
+    wl.lon_s, wl.lat_s = lon.cpu().numpy(), lat.cpu().numpy()
+    wl.data = data.cpu().numpy()
+    wl.lon_t, wl.lat_t = lon_t, lat_t
+    wl.omega, wl.support = None, support
+    wl.n_targets = lon_t.size
+    return wl
+
+
+def test_paper_example1_full_sampled():
+    """The paper's Example 1 at 1e8 samples (few targets, many samples: the
+    FP32 gridder splits each tile's candidates over many CTAs)."""
+    import torch
+    from paper_1604_06667_gb300 import Gridder
+    lon, lat, data, lon_t, lat_t, kern, support, maxres = workloads.example1_device("cuda")
+    g = Gridder(lon_t, lat_t, n_channels=1)
+    g.set_kernel("gauss1d", (kern["sigma"],), support, maxres)
+    w = torch.empty(lon_t.size, device="cuda")
+    out = g.grid_oneshot(lon, lat, data, out_weights=w)
+    g.sync()
+    out_np, w_np = out.cpu().numpy(), w.cpu().numpy()
+    g.close()
+    wl = _host_wl(lon, lat, data, lon_t, lat_t, kern, support)
+    del lon, lat, data
+    tsel = np.unique(np.concatenate([_sampled_targets(wl, 24, 607), [0, lon_t.size - 1]]))
+    ref, _ = oracle_on_targets(wl, tsel, oracle.gauss1d(kern["sigma"], support))
+    compare_maps(out_np[tsel], w_np[tsel], ref, tol=FP32_TOL)

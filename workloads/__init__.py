@@ -326,3 +326,29 @@ def batch_job_device(spec: dict, device, dtype_override=None):
         data += prof[:, None] * amp[None, :]
     lon_t, lat_t = car_grid(spec["lon0"], spec["lat0"], side, side, step)
     return lon, lat, data, lon_t, lat_t
+
+
+# ---------------------------------------------------------------------------
+# The paper's Example 1 (Sect. 4): random samples onto a 5 x 5 deg field
+# ---------------------------------------------------------------------------
+ARCSEC = 1.0 / 3600.0
+
+
+def example1_device(device, n: int = 100_000_000, seed: int | None = None):
+    """n samples uniform in a 5 deg x 5 deg field at (30, 0), one channel of
+    N(0, 1) noise, gridded onto 200" pixels (90 x 90) with a Gaussian of FWHM
+    300" (support 3 sigma, hpx_maxres sigma / 2).  Drawn on the device with a
+    seeded torch generator (1e8 samples).  Returns (lon, lat, data[n, 1],
+    lon_t, lat_t, kernel dict, support, hpx_maxres)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE + 6 if seed is None else seed)
+    side, lon0, lat0 = 5.0, 30.0, 0.0
+    lon = lon0 + (torch.rand(n, generator=gen, device=device, dtype=torch.float64) - 0.5) * side
+    lat = lat0 + (torch.rand(n, generator=gen, device=device, dtype=torch.float64) - 0.5) * side
+    data = torch.randn((n, 1), generator=gen, device=device, dtype=torch.float32)
+    npx = int(round(side / (200.0 * ARCSEC)))
+    lon_t, lat_t = car_grid(lon0, lat0, npx, npx, 200.0 * ARCSEC)
+    sigma = 300.0 * ARCSEC / math.sqrt(8.0 * math.log(2.0))
+    return lon, lat, data, lon_t, lat_t, {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, \
+        sigma / 2.0

@@ -428,6 +428,53 @@ def time_batched(args, dev, n_jobs=64):
     return res
 
 
+def time_config(args, dev, name):
+    """Plain 2-D (2e4 samples -> 100^2, sigma 2.5') and all-sky elliptical
+    (1e7 samples x 32 channels -> 4096 x 2048, 10'/6'/PA 30, r = 30')
+    one-shot calls, each form timed with CUDA events after warm-up."""
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder, _capi
+    wl = workloads.plain2d(1.0) if name == "plain2d" else workloads.allsky(1.0)
+    lon = torch.from_numpy(wl.lon_s).to(dev)
+    lat = torch.from_numpy(wl.lat_s).to(dev)
+    d32 = torch.from_numpy(wl.data).to(dev)
+    k = wl.kernel
+    kt, kp = ("gauss1d", (k["sigma"],)) if k["type"] == "gauss1d" else \
+        ("gauss2d", (k["smaj"], k["smin"], k["pa"]))
+    g = Gridder(wl.lon_t, wl.lat_t, n_channels=wl.n_channels, device=dev)
+    g.set_kernel(kt, kp, wl.support, wl.hpx_maxres)
+    out = torch.empty((wl.n_targets, wl.n_channels), device=dev)
+    w = torch.empty(wl.n_targets, device=dev)
+    forms = [("fp32", _capi.CG_PATH_FP32, d32)]
+    if wl.n_channels % 8 == 0:
+        forms.append(("bf16", _capi.CG_PATH_TC, d32.to(torch.bfloat16)))
+    res = {"workload": "%s: %d samples x %d channels -> %d targets" % (
+        name, wl.n_samples, wl.n_channels, wl.n_targets)}
+    stream = torch.cuda.current_stream(dev)
+    for form, path, d in forms:
+        g.set_path(path)
+        for _ in range(3):
+            g.grid_oneshot(lon, lat, d, out=out, out_weights=w)
+        g.sync()
+        pairs = g.info()["n_pairs"]
+        steps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.grid_oneshot(lon, lat, d, out=out, out_weights=w)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        db = 2 if form == "bf16" else 4
+        nbytes = wl.n_samples * (16 + wl.n_channels * db) + wl.n_targets * (4 * wl.n_channels + 4)
+        res[form] = {"ms_per_call": ms, "pairs": pairs,
+                     "updates_per_s": pairs * wl.n_channels / (ms / 1e3),
+                     "hbm_frac": nbytes / (ms / 1e3) / (load_peaks()[0]["hbm_gbs"] * 1e9)}
+    g.close()
+    return res
+
+
 def time_example1(args, dev):
     """The paper's Example 1 (Sect. 4) at 1e8 samples: 5 x 5 deg field, 200"
     pixels, FWHM 300" Gaussian, one channel of noise -- the paper quotes about
@@ -538,6 +585,9 @@ def main():
         line["batched"] = time_batched(args, dev)
         progress("paper example 1")
         line["paper_example1"] = time_example1(args, dev)
+        progress("plain 2-D and all-sky")
+        line["plain2d"] = time_config(args, dev, "plain2d")
+        line["allsky"] = time_config(args, dev, "allsky")
 
     # ---- end to end: pinned host inputs, copies inside the timed region ----
     if not args.no_e2e:

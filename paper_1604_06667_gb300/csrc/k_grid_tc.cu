@@ -58,9 +58,12 @@ constexpr int kWW = 8;              // weight warps (2 per TMEM lane quarter)
 constexpr int kGPW = 2;             // groups of 8 candidates per weight warp and chunk
 static_assert(kGPW * 8 * (kWW / 4) == 32, "weight warps cover a chunk");
 constexpr int kNP = 8;              // producer warps (chunk q goes to warp q % kNP)
-constexpr int kThreads = (kWW + kNP + 1) * 32;
+constexpr int kEW = 4;              // epilogue warps (one per TMEM lane quarter)
+constexpr int kThreads = (kWW + kNP + kEW + 1) * 32;
 constexpr int kProdWarp = kWW;      // first producer warp
-constexpr int kMmaWarp = kWW + kNP;
+constexpr int kEpiWarp = kWW + kNP; // first epilogue warp
+constexpr int kMmaWarp = kWW + kNP + kEW;
+constexpr int kEpiPitch = 36;       // floats per row of an epilogue tile (32 + pad)
 constexpr int kNS = 8;             // pipeline stages (one per producer warp)
 constexpr int kMaxStages = kNS;
 // a wait gives up after ~1 s of SM clock (or at once after another role gave up)
@@ -111,14 +114,16 @@ struct Smem {
   float* reach;        // ns x 4 quarters x kK: squared chord to the quarter centre
   uint32_t* cidx;      // ns x kK: row of the caller's arrays
   float2* wpart;       // 2 buffers x (kWW / 4) groups x kT partial weight sums
+  float* epi;          // kEW x 32 x kEpiPitch: epilogue transpose tiles
   uint64_t* full;      // ns: data rows landed (TMA transaction bytes)
   uint64_t* cfull;     // ns: candidate vectors written
   uint64_t* afull;     // ns: weights in TMEM
   uint64_t* empty;     // ns: MMAs of the stage done
-  uint64_t* dfull;
-  uint64_t* dempty;
+  uint64_t* dfull;     // the item's MMAs are complete (D ready)
+  uint64_t* dempty;    // the epilogue has drained D
   uint64_t* fin;
-  uint64_t* wbar;
+  uint64_t* wfull;     // 2: the weight warps' W partials of an item are written
+  uint64_t* wempty;    // 2: the epilogue has read them
   uint32_t* tmem_base;
   int* abort_flag;
 };
@@ -372,6 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     p += (size_t)ns * kK * sizeof(uint32_t);
     S.wpart = reinterpret_cast<float2*>(p);
     p += (size_t)2 * (kWW / 4) * kT * sizeof(float2);
+    S.epi = reinterpret_cast<float*>(p);
+    p += (size_t)kEW * 32 * kEpiPitch * sizeof(float);
     S.full = reinterpret_cast<uint64_t*>(p);
     S.cfull = S.full + kMaxStages;
     S.afull = S.cfull + kMaxStages;
@@ -379,8 +386,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     S.dfull = S.empty + kMaxStages;
     S.dempty = S.dfull + 1;
     S.fin = S.dempty + 1;
-    S.wbar = S.fin + 1;
-    S.tmem_base = reinterpret_cast<uint32_t*>(S.wbar + 1);
+    S.wfull = S.fin + 1;
+    S.wempty = S.wfull + 2;
+    S.tmem_base = reinterpret_cast<uint32_t*>(S.wempty + 2);
     S.abort_flag = reinterpret_cast<int*>(S.tmem_base + 1);
   }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -399,9 +407,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       mbar_init(&S.empty[s], 1);         // MMA commit
     }
     mbar_init(S.dfull, 1);
-    mbar_init(S.dempty, kWW * 32);
+    mbar_init(S.dempty, kEW * 32);
     mbar_init(S.fin, 1);
-    mbar_init(S.wbar, kWW * 32);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.wfull[b], kWW * 32);
+      mbar_init(&S.wempty[b], kEW * 32);
+    }
     *S.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -487,6 +498,118 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       q += kNP;
       if (item < n_items) fetch_chunk(a, item, ch, lane, f);
     }
+  } else if (warp >= kEpiWarp && warp < kEpiWarp + kEW) {
+    // ------------------------------------------------------------ epilogue
+    // W from the weight warps' partials; once the item's MMAs are complete,
+    // D (this quarter's 32 TMEM lanes, all slab columns) is normalised and
+    // written; then D is released to the next item's MMAs.
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    constexpr int kGroups = kWW / 4;
+    uint32_t tq = 0;
+    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+      const int64_t tile = item / a.n_slabs;
+      const int slab = (int)(item % a.n_slabs);
+      const int c_base = slab * cp;
+      const int64_t slot = tile * kT + row;
+      const uint32_t user = a.perm_t[slot];
+      const int nch = chunks_of(a, item);
+      const int wb = (int)(tq & 1);
+      if (!mbar_wait(&S.wfull[wb], (tq >> 1) & 1, abort_flag)) {
+        set_error(a.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      float W = 0.f;
+#pragma unroll
+      for (int g2 = 0; g2 < kGroups; ++g2) {
+        const float2 o = S.wpart[((size_t)wb * kGroups + g2) * kT + row];
+        W += o.x + o.y;
+      }
+      mbar_arrive(&S.wempty[wb]);
+      if (!mbar_wait(S.dfull, tq & 1, abort_flag)) {
+        set_error(a.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      bool valid = user != 0xffffffffu;
+      if (valid && (int64_t)user >= a.P) {  // never expected: record and skip
+        set_error(a.err, ERR_INTERNAL);
+        valid = false;
+      }
+      const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
+      // one-shot output: 32 x 32 blocks through a padded shared tile so that
+      // every store instruction writes 4 whole 128-byte rows
+      const bool fast = a.mode == 2 && (a.C & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+      float* tile_s = S.epi + (size_t)(warp - kEpiWarp) * 32 * kEpiPitch;
+      for (int cb = 0; cb < cp; cb += 32) {
+        const int c0 = c_base + cb;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t r[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(tmem_d + lane_off + (uint32_t)(cb + 16 * h)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int c1 = c0 + 16 * h;
+          if (fast) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(tile_s + lane * kEpiPitch + 16 * h + j) =
+                  make_float4(nch ? __uint_as_float(r[j]) * invW : invW,
+                              nch ? __uint_as_float(r[j + 1]) * invW : invW,
+                              nch ? __uint_as_float(r[j + 2]) * invW : invW,
+                              nch ? __uint_as_float(r[j + 3]) * invW : invW);
+          } else if (valid && a.mode == 2) {
+            float* dst = a.out + (size_t)user * a.C + c1;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c1 + j < a.C) dst[j] = nch ? __uint_as_float(r[j]) * invW : invW;
+          } else if (valid) {
+            float* dst = a.acc_num + (size_t)slot * a.C + c1;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (c1 + j >= a.C) continue;
+              const float v = nch ? __uint_as_float(r[j]) : 0.f;
+              dst[j] = (a.mode == 1) ? dst[j] + v : v;
+            }
+          }
+        }
+        if (!fast) continue;
+        __syncwarp();
+        // lane: row 4 k + lane / 8 of the block, columns 4 (lane % 8) .. + 3
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int rr = 4 * k + (lane >> 3);
+          const int cc = 4 * (lane & 7);
+          const uint32_t u = __shfl_sync(0xffffffffu, valid ? user : 0xffffffffu, rr);
+          const float4 v = *reinterpret_cast<const float4*>(tile_s + rr * kEpiPitch + cc);
+          if (u != 0xffffffffu && c0 + cc < a.C)
+            *reinterpret_cast<float4*>(a.out + (size_t)u * a.C + c0 + cc) = v;
+        }
+        __syncwarp();
+      }
+      if (valid && slab == 0) {
+        if (a.mode == 2) {
+          if (a.out_w) a.out_w[user] = W;
+        } else {
+          float2 old = (a.mode == 1) ? a.acc_w[slot] : make_float2(0.f, 0.f);
+          const float t = old.x + W;
+          const float bp = t - old.x;
+          const float err = (old.x - (t - bp)) + (W - bp);
+          a.acc_w[slot] = make_float2(t, old.y + err);
+        }
+      }
+      fence_before();
+      mbar_arrive(S.dempty);
+    }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -555,7 +678,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int row = quarter * 32 + lane;      // TMEM lane = target row
     const int grp = warp >> 2;                // candidates 16 grp .. 16 grp + 15
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const int part_cols = cp / (kWW / 4);     // epilogue columns of this warp
     const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
     PairConst P;
     P.q1 = a.kd.k1;
@@ -583,7 +705,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         f1 = a.f1[slot];
         f2 = a.f2[slot];
       }
-      const uint32_t user = a.perm_t[slot];
       const int nch = chunks_of(a, item);
       // the quarter's reach: candidates beyond (quarter radius + r) give w = 0
       const float4 sq = a.subf[tile * 4 + quarter];
@@ -599,8 +720,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         // ---- 2 x 8 weights of this thread's row, branch-free ----
         // lanes 0-15 test one candidate each against the quarter's reach;
-        // a group of 8 with none in reach is skipped, two live groups are
-        // evaluated as one 16-pair block (more independent work in flight)
+        // a group of 8 with none in reach is skipped
         const int kb = st * kK + grp * 16;
         bool reach = false;
         if (lane < 16) reach = S.reach[(st * 4 + quarter) * kK + grp * 16 + lane] <= reach2;
@@ -608,14 +728,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         float w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0.f;
-        if ((live & 0xffu) && (live & 0xff00u)) {
-          eval_pairs<16, KT, BIG>(S.cand + kb, S.cidx + kb, at, f1, f2, P, a, slot, w, np_item);
-        } else if (live & 0xffu) {
+        if (live & 0xffu)
           eval_pairs<8, KT, BIG>(S.cand + kb, S.cidx + kb, at, f1, f2, P, a, slot, w, np_item);
-        } else if (live & 0xff00u) {
+        if (live & 0xff00u)
           eval_pairs<8, KT, BIG>(S.cand + kb + 8, S.cidx + kb + 8, at, f1, f2, P, a, slot, w + 8,
                                  np_item);
-        }
         uint32_t packed[8], packed_lo[8];
         float part = 0.f;
 #pragma unroll
@@ -667,79 +784,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         mbar_arrive(&S.afull[st]);
       }
       if (slab == 0) npair += np_item;
-      // ---- epilogue: combine the weight-map partials of this row ----
+      // ---- hand this row's weight-map partial to the epilogue warps ----
       constexpr int kGroups = kWW / 4;
-      float2* wp = S.wpart + (size_t)(tq & 1) * kGroups * kT;   // double buffered
-      wp[grp * kT + row] = make_float2(ws, wc);
-      mbar_arrive(S.wbar);
-      if (!mbar_wait(S.wbar, tq & 1, abort_flag)) ok = false;
-      float W = 0.f;
-#pragma unroll
-      for (int g2 = 0; g2 < kGroups; ++g2) {
-        const float2 o = wp[g2 * kT + row];
-        W += o.x + o.y;
-      }
-      // ---- wait for this tile's MMAs ----
-      if (!ok || !mbar_wait(S.dfull, tq & 1, abort_flag)) {
+      const int wb = (int)(tq & 1);
+      if (ok && tq >= 2 && !mbar_wait(&S.wempty[wb], ((tq >> 1) - 1) & 1, abort_flag)) ok = false;
+      if (!ok) {
         set_error(a.err, ERR_TIMEOUT);
         *abort_flag = 1;
         break;
       }
-      fence_after();
-      bool valid = user != 0xffffffffu;
-      if (valid && (int64_t)user >= a.P) {  // never expected: record and skip
-        set_error(a.err, ERR_INTERNAL);
-        valid = false;
-      }
-      const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
-      for (int cb = grp * part_cols; cb < (grp + 1) * part_cols; cb += 16) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tmem_d + lane_off + (uint32_t)cb));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!valid) continue;
-        const int c0 = c_base + cb;
-        if (a.mode == 2) {
-          float* dst = a.out + (size_t)user * a.C + c0;
-          if (c0 + 16 <= a.C && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-              float4 v = make_float4(nch ? __uint_as_float(r[j]) * invW : invW,
-                                     nch ? __uint_as_float(r[j + 1]) * invW : invW,
-                                     nch ? __uint_as_float(r[j + 2]) * invW : invW,
-                                     nch ? __uint_as_float(r[j + 3]) * invW : invW);
-              *reinterpret_cast<float4*>(dst + j) = v;
-            }
-          } else {
-            for (int j = 0; j < 16 && c0 + j < a.C; ++j)
-              dst[j] = nch ? __uint_as_float(r[j]) * invW : invW;
-          }
-        } else {
-          float* dst = a.acc_num + (size_t)slot * a.C + c0;
-          for (int j = 0; j < 16 && c0 + j < a.C; ++j) {
-            const float v = nch ? __uint_as_float(r[j]) : 0.f;
-            dst[j] = (a.mode == 1) ? dst[j] + v : v;
-          }
-        }
-      }
-      if (valid && slab == 0 && grp == 0) {
-        if (a.mode == 2) {
-          if (a.out_w) a.out_w[user] = W;
-        } else {
-          float2 old = (a.mode == 1) ? a.acc_w[slot] : make_float2(0.f, 0.f);
-          const float t = old.x + W;
-          const float bp = t - old.x;
-          const float err = (old.x - (t - bp)) + (W - bp);
-          a.acc_w[slot] = make_float2(t, old.y + err);
-        }
-      }
-      fence_before();
-      mbar_arrive(S.dempty);
+      S.wpart[((size_t)wb * kGroups + grp) * kT + row] = make_float2(ws, wc);
+      mbar_arrive(&S.wfull[wb]);
     }
     unsigned c = npair;
 #pragma unroll
@@ -771,7 +826,8 @@ KernFn pick_kernel(int kt, bool split, bool big) {
 
 size_t smem_bytes(int cp, int ns) {
   return (size_t)ns * cp * 64 + (size_t)ns * kK * (sizeof(float4) + 4 * sizeof(float) + sizeof(uint32_t)) +
-         (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (4 * kMaxStages + 4) * sizeof(uint64_t) +
+         (size_t)2 * (kWW / 4) * kT * sizeof(float2) + (size_t)kEW * 32 * kEpiPitch * 4 +
+         (4 * kMaxStages + 7) * sizeof(uint64_t) +
          16;
 }
 

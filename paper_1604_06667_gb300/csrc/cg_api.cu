@@ -106,6 +106,8 @@ void free_all(cg_grid* g) {
   dfree(g->sw.vals_alt, s);
   dfree(g->sw.hist, s);
   dfree(g->sw.totals, s);
+  dfree(g->sw.status, s);
+  dfree(g->sw.os_meta, s);
   dfree(g->s_hi, s);
   dfree(g->s_lo, s);
   dfree(g->u_hi, s);
@@ -125,6 +127,8 @@ void free_all(cg_grid* g) {
   dfree(g->tix_sw.vals_alt, s);
   dfree(g->tix_sw.hist, s);
   dfree(g->tix_sw.totals, s);
+  dfree(g->tix_sw.status, s);
+  dfree(g->tix_sw.os_meta, s);
   dfree(g->ds_num, s);
   dfree(g->ds_w, s);
   dfree(g->ds_num0, s);

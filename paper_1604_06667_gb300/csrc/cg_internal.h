@@ -66,6 +66,12 @@ struct SortWork {         // radix-sort scratch
   uint32_t* hist = nullptr;     // [256 * nblk]
   uint32_t* totals = nullptr;   // [256]
   size_t cap_n = 0, cap_hist = 0, key_bytes = 0;
+  // one-sweep passes (32-bit keys)
+  uint64_t* status = nullptr;   // [nblk * 256] epoch-tagged look-back words
+  uint32_t* os_meta = nullptr;  // digit totals [4][256] + tickets [4]
+  size_t cap_status = 0;
+  uint32_t epoch = 0;
+  unsigned* err = nullptr;      // device error word for bounded waits
 };
 
 }  // namespace cg

@@ -359,10 +359,11 @@ cudaError_t target_index_build(cg_grid* g) {
   g->n_launches += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int bits = key_bits_for(g->nside);
+  g->tix_sw.err = g->d_err;
   if ((e = radix_sort_u32(g->tix_key, g->tix_val, m, bits, g->tix_sw, s, &g->tix_skey,
                           &g->tix_sslot)) != cudaSuccess)
     return e;
-  g->n_launches += 3 * ((bits + 7) / 8);
+  g->n_launches += 1 + (bits + 7) / 8;
   if ((e = sorted_gather(g->nside, g->tix_skey, g->tix_sslot, g->tix_uhi, g->tix_ulo, m,
                          g->tix_hi, g->tix_lo, g->tix_ring_off, s)) != cudaSuccess)
     return e;

@@ -344,7 +344,8 @@ cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const
 
 cudaError_t samples_sort(cg_grid* g, int64_t n) {
   const int bits = key_bits_for(g->nside);
-  g->n_launches += 3 * ((bits + 7) / 8);
+  g->n_launches += 1 + (bits + 7) / 8;
+  g->sw.err = g->d_err;
   return radix_sort_u32(g->key, g->val, n, bits, g->sw, g->stream, &g->sorted_key,
                         &g->sorted_val);
 }

@@ -11,6 +11,8 @@
 //              offset by the count of all smaller digits;
 //   k_scatter  each block ranks its keys stably (round by round, warp-level
 //              match for equal digits, warps in order) and writes them out.
+#include <algorithm>
+
 #include "cg_common.cuh"
 #include "cg_internal.h"
 
@@ -215,12 +217,197 @@ cudaError_t radix_sort_impl(K* keys, uint32_t* vals, int64_t n, int key_bits, So
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// One-sweep passes (32-bit keys): a tile's digit offsets come from the global
+// digit totals (order-independent, one histogram kernel for every pass) plus
+// the counts of the tiles before it, found by decoupled look-back: each tile
+// publishes its per-digit count, then its inclusive prefix, in one 64-bit
+// status word per (tile, digit) tagged with the sort's epoch (no clearing
+// between sorts).  Tiles take tickets in launch order, so a tile only waits
+// for tiles that already run; every wait is bounded and records an error.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 4;
+constexpr uint64_t kAgg = 1, kInc = 2;
+constexpr int kOsItems = 16;                      // keys per thread of a one-sweep tile
+constexpr int kOsTile = kThreads * kOsItems;
+
+__global__ void __launch_bounds__(kThreads) k_os_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                                     int npass, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kMaxPasses][kRadix];
+  for (int p = 0; p < kMaxPasses; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < npass; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&ghist[p * kRadix + threadIdx.x], h[p][threadIdx.x]);
+}
+
+__device__ __forceinline__ uint64_t os_word(uint32_t epoch, uint64_t kind, uint32_t v) {
+  return ((uint64_t)epoch << 34) | (kind << 32) | v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_os_pass(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+    const uint32_t* __restrict__ ghist, uint64_t* status, uint32_t* ticket, uint32_t epoch,
+    unsigned* err) {
+  __shared__ uint32_t s_b;
+  __shared__ uint32_t blk_off[kRadix];
+  __shared__ uint32_t cnt[kRadix];
+  __shared__ uint32_t wcnt[kWarps][kRadix];
+  __shared__ uint32_t run[kRadix];
+  __shared__ uint32_t warp_sums[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_b = atomicAdd(ticket, 1u);
+  cnt[tid] = 0;
+  run[tid] = 0;
+  __syncthreads();
+  const int64_t b = s_b;
+  const int64_t base = b * kOsTile;
+  // this tile's digit counts
+  uint32_t k_it[kOsItems], v_it[kOsItems];
+#pragma unroll
+  for (int it = 0; it < kOsItems; ++it) {
+    const int64_t i = base + (int64_t)it * kThreads + tid;
+    k_it[it] = 0;
+    v_it[it] = 0;
+    if (i < n) {
+      k_it[it] = kin[i];
+      v_it[it] = vin[i];
+      atomicAdd(&cnt[(k_it[it] >> shift) & 0xffu], 1u);
+    }
+  }
+  __syncthreads();
+  // global exclusive offset of digit tid
+  uint32_t tot;
+  const uint32_t g_excl = block_exclusive_scan(ghist[tid], warp_sums, tot);
+  // publish the count, look back for the prefix, publish the prefix
+  const uint32_t c = cnt[tid];
+  volatile uint64_t* st = status;
+  if (b == 0) {
+    st[(size_t)tid] = os_word(epoch, kInc, c);
+    blk_off[tid] = g_excl;
+  } else {
+    st[(size_t)b * kRadix + tid] = os_word(epoch, kAgg, c);
+    // look back 8 predecessors per step (independent loads), summing in order
+    // until an inclusive prefix; a predecessor not yet published is re-read
+    uint32_t prefix = 0;
+    int64_t j = b - 1;
+    uint32_t spins = 0;
+    const long long t0 = clock64();
+    bool done = false;
+    while (j >= 0 && !done) {
+      uint64_t wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wv[q] = (j - q >= 0) ? st[(size_t)(j - q) * kRadix + tid] : 0;
+      int q = 0;
+      for (; q < 8 && j - q >= 0; ++q) {
+        const uint64_t w = wv[q];
+        const uint64_t kind = (w >> 32) & 3u;
+        if ((uint32_t)(w >> 34) != epoch || kind == 0) break;   // not ready yet
+        prefix += (uint32_t)w;
+        if (kind == kInc) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      j -= q;
+      if (q < 8 && j >= 0) {
+        // never expected to take long: give up after ~1 s and record it
+        if ((++spins & 63u) == 0 && clock64() - t0 > 2000000000LL) {
+          set_error(err, ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    st[(size_t)b * kRadix + tid] = os_word(epoch, kInc, prefix + c);
+    blk_off[tid] = g_excl + prefix;
+  }
+  __syncthreads();
+  // stable ranks in (item, thread) order and scatter
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int it = 0; it < kOsItems; ++it) {
+    const int64_t i = base + (int64_t)it * kThreads + tid;
+    const bool valid = i < n;
+    const unsigned d = valid ? ((k_it[it] >> shift) & 0xffu) : (unsigned)kRadix;
+#pragma unroll
+    for (int w2 = 0; w2 < kWarps; ++w2) wcnt[w2][tid] = 0;
+    __syncthreads();
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t r = run[tid];
+#pragma unroll
+      for (int w2 = 0; w2 < kWarps; ++w2) {
+        const uint32_t cc = wcnt[w2][tid];
+        wcnt[w2][tid] = r;
+        r += cc;
+      }
+      run[tid] = r;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = blk_off[d] + wcnt[wid][d] + rank;
+      kout[pos] = k_it[it];
+      vout[pos] = v_it[it];
+    }
+    __syncthreads();   // wcnt is cleared for the next item
+  }
+}
+
 }  // namespace
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
                            SortWork& w, cudaStream_t s, uint32_t** out_keys,
                            uint32_t** out_vals) {
-  return radix_sort_impl<uint32_t>(keys, vals, n, key_bits, w, s, out_keys, out_vals);
+  *out_keys = keys;
+  *out_vals = vals;
+  if (n <= 0) return cudaSuccess;
+  const int npass = (key_bits + 7) / 8;
+  const int nblk = (int)ceil_div(n, kOsTile);
+  cudaError_t e = ensure_work<uint32_t>(w, n, (int)ceil_div(n, kTileKeys), s);
+  if (e != cudaSuccess) return e;
+  if (w.cap_status < (size_t)nblk * kRadix) {
+    dfree(w.status, s);
+    w.cap_status = 0;
+    if ((e = dalloc(&w.status, (size_t)nblk * kRadix, s)) != cudaSuccess) return e;
+    // a fresh array holds no word of a live epoch
+    if ((e = cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * (size_t)nblk * kRadix, s)) !=
+        cudaSuccess)
+      return e;
+    w.cap_status = (size_t)nblk * kRadix;
+  }
+  if (!w.os_meta) {
+    if ((e = dalloc(&w.os_meta, (size_t)(kMaxPasses * kRadix + kMaxPasses), s)) != cudaSuccess)
+      return e;
+  }
+  uint32_t* ghist = w.os_meta;
+  uint32_t* tickets = w.os_meta + kMaxPasses * kRadix;
+  e = cudaMemsetAsync(w.os_meta, 0, sizeof(uint32_t) * (kMaxPasses * kRadix + kMaxPasses), s);
+  if (e != cudaSuccess) return e;
+  const int hblk = (int)std::min<int64_t>(ceil_div(n, kThreads * 8), 1024);
+  k_os_hist<<<hblk, kThreads, 0, s>>>(keys, n, npass, ghist);
+  uint32_t *kin = keys, *kout = static_cast<uint32_t*>(w.keys_alt);
+  uint32_t *vin = vals, *vout = w.vals_alt;
+  for (int p = 0; p < npass; ++p) {
+    w.epoch = (w.epoch + 1) & 0x3fffffffu;
+    if (w.epoch == 0) w.epoch = 1;
+    k_os_pass<<<nblk, kThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p, ghist + p * kRadix,
+                                        w.status, tickets + p, w.epoch, w.err);
+    uint32_t* tk = kin; kin = kout; kout = tk;
+    uint32_t* tv = vin; vin = vout; vout = tv;
+  }
+  *out_keys = kin;
+  *out_vals = vin;
+  return cudaGetLastError();
 }
 
 // Same passes as radix_sort_u32 on caller-provided scratch (no allocation):

@@ -547,37 +547,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       float* tile_s = S.epi + (size_t)(warp - kEpiWarp) * 32 * kEpiPitch;
       for (int cb = 0; cb < cp; cb += 32) {
         const int c0 = c_base + cb;
+        // both 16-column loads in flight before one wait
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem_d + lane_off + (uint32_t)cb));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(tmem_d + lane_off + (uint32_t)(cb + 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          uint32_t r[16];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-              : "r"(tmem_d + lane_off + (uint32_t)(cb + 16 * h)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           const int c1 = c0 + 16 * h;
           if (fast) {
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
               *reinterpret_cast<float4*>(tile_s + lane * kEpiPitch + 16 * h + j) =
-                  make_float4(nch ? __uint_as_float(r[j]) * invW : invW,
-                              nch ? __uint_as_float(r[j + 1]) * invW : invW,
-                              nch ? __uint_as_float(r[j + 2]) * invW : invW,
-                              nch ? __uint_as_float(r[j + 3]) * invW : invW);
+                  make_float4(nch ? __uint_as_float(r[16 * h + j]) * invW : invW,
+                              nch ? __uint_as_float(r[16 * h + j + 1]) * invW : invW,
+                              nch ? __uint_as_float(r[16 * h + j + 2]) * invW : invW,
+                              nch ? __uint_as_float(r[16 * h + j + 3]) * invW : invW);
           } else if (valid && a.mode == 2) {
             float* dst = a.out + (size_t)user * a.C + c1;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (c1 + j < a.C) dst[j] = nch ? __uint_as_float(r[j]) * invW : invW;
+              if (c1 + j < a.C) dst[j] = nch ? __uint_as_float(r[16 * h + j]) * invW : invW;
           } else if (valid) {
             float* dst = a.acc_num + (size_t)slot * a.C + c1;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               if (c1 + j >= a.C) continue;
-              const float v = nch ? __uint_as_float(r[j]) : 0.f;
+              const float v = nch ? __uint_as_float(r[16 * h + j]) : 0.f;
               dst[j] = (a.mode == 1) ? dst[j] + v : v;
             }
           }

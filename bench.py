@@ -358,8 +358,8 @@ def time_differentiable(args, dev):
 # ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (summary under
 # profiles/); valid only for the kernel source it was taken with.
 TRAFFIC_CAPTURE = {"source": "paper_1604_06667_gb300/csrc/k_grid_tc.cu",
-                   "sha256": "c0e431261b9d124009d2fea838e181e19bd6f1e2825e487fb4dd08991f36c970",
-                   "bytes_per_launch": 864511232 + 274457088}
+                   "sha256": "d1d58f8e04b0a54fc1cf9da6324a68f4f51e5bf7dbcf07ede01e8219f066836b",
+                   "bytes_per_launch": 910251520 + 257925632}
 
 
 def captured_traffic():

@@ -26,18 +26,22 @@
 // one warp per SM, ~13 TB/s from L2 with eight); hence eight producer warps.
 //
 // Warp roles (persistent CTA, static round-robin over (tile, slab) items):
-//   warps 0-7  weights: warp w handles target rows 32 (w % 4) .. + 31 (one
-//              TMEM lane quarter, a compact 32-target k-d leaf) and candidates
-//              16 (w / 4) .. + 15 of every chunk, as two groups of 8; a group
-//              that cannot reach the quarter (disc of radius quarter radius +
-//              r) is skipped; weight-map sums; epilogue (the quarter's columns
-//              split two ways);
-//   warps 8-15 producers (chunk q belongs to warp q % 8, which owns stage
-//              q % 8): locate the chunk's candidates in the tile's sample
-//              ranges, write their tile-relative vectors, gather their data
-//              rows; the next own chunk's loads are issued before waiting for
-//              the stage to be free;
-//   warp 16    MMA issue (one lane) and tcgen05.commit.
+//   warps 0-7   weights: warp w handles target rows 32 (w % 4) .. + 31 (one
+//               TMEM lane quarter, a compact 32-target k-d leaf) and
+//               candidates 16 (w / 4) .. + 15 of every chunk, as two groups of
+//               8; a group that cannot reach the quarter (disc of radius
+//               quarter radius + r) is skipped; the FP32 arithmetic runs on
+//               pairs of candidates with the packed f32x2 instructions;
+//               weight-map partial sums (compensated) per item;
+//   warps 8-15  producers (chunk q belongs to warp q % 8, which owns stage
+//               q % 8): locate the chunk's candidates in the tile's sample
+//               ranges, write their tile-relative vectors, gather their data
+//               rows; the next own chunk's loads are issued before waiting
+//               for the stage to be free;
+//   warps 16-19 epilogue (one per TMEM lane quarter): W from the weight
+//               warps' partials, D -> registers -> R = N / W (or the
+//               accumulators), then D is released to the next item;
+//   warp 20     MMA issue (one lane) and tcgen05.commit.
 // Every mbarrier wait is bounded; on time-out the kernel records
 // ERR_TIMEOUT, stops issuing work, waits for its own MMAs and frees TMEM.
 #include <cuda.h>
@@ -80,6 +84,7 @@ struct TcArgs {
   const int2* range_s;
   const int32_t* range_c;
   const int32_t* tile_cand;
+  const int32_t* order;  // items by decreasing cost (null: round-robin over item indices)
   int64_t n_tiles;
   const float4* f1;
   const float4* f2;
@@ -110,7 +115,7 @@ struct TcArgs {
 
 struct Smem {
   uint8_t* B;          // ns stages of cp * 64 bytes
-  float4* cand;        // ns x kK: tile-relative vector, w = log2(omega)
+  float* cand;         // ns x kK/2 pairs x 8: (x0 x1 y0 y1) (z0 z1 l0 l1), l = log2 omega + e_mid
   float* reach;        // ns x 4 quarters x kK: squared chord to the quarter centre
   uint32_t* cidx;      // ns x kK: row of the caller's arrays
   float2* wpart;       // 2 buffers x (kWW / 4) groups x kT partial weight sums
@@ -197,6 +202,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo,
   return smem_desc(addr, lbo, sbo) | ((uint64_t)2 << 61);  // layout: 128-byte swizzle
 }
 
+// Item k of this CTA's sequence, -1 past its end.  With an order (items
+// ranked by decreasing cost), round k deals ranks k G .. k G + G - 1 to the G
+// CTAs, forwards on even rounds and backwards on odd ones, so every CTA gets
+// a similar total; without one, CTA b takes items b, b + G, b + 2 G, ...
+__device__ __forceinline__ int64_t item_at(const TcArgs& a, int64_t n_items, int64_t k) {
+  const int64_t G = gridDim.x;
+  if (!a.order) {
+    const int64_t it = (int64_t)blockIdx.x + k * G;
+    return it < n_items ? it : -1;
+  }
+  const int64_t pos = k * G + ((k & 1) ? G - 1 - (int64_t)blockIdx.x : (int64_t)blockIdx.x);
+  return pos < n_items ? (int64_t)a.order[pos] : -1;
+}
+
 __device__ __forceinline__ int chunks_of(const TcArgs& a, int64_t item) {
   return (a.tile_cand[item / a.n_slabs] + kK - 1) / kK;
 }
@@ -274,87 +293,152 @@ __device__ __forceinline__ void fetch_chunk(const TcArgs& a, int64_t item, int c
 }
 
 // Next own chunk: global chunk q + kNP, i.e. kNP chunks further along the
-// CTA's sequence of (item, chunk) pairs.
-__device__ __forceinline__ void advance(const TcArgs& a, int64_t n_items, int64_t& item, int& ch,
-                                        int& nch, int step) {
+// CTA's sequence of (item, chunk) pairs; item k of the sequence is `item`.
+__device__ __forceinline__ void advance(const TcArgs& a, int64_t n_items, int64_t& k,
+                                        int64_t& item, int& ch, int& nch, int step) {
   ch += step;
-  while (item < n_items && ch >= nch) {
+  while (item >= 0 && ch >= nch) {
     ch -= nch;
-    item += gridDim.x;
-    nch = (item < n_items) ? chunks_of(a, item) : 0;
+    item = item_at(a, n_items, ++k);
+    nch = (item >= 0) ? chunks_of(a, item) : 0;
   }
 }
 
-// Constants of the weight evaluation (per kernel launch).
+// Constants of the weight evaluation (per kernel launch).  The squared chord
+// is carried as x = c2 - mid, mid the centre of the guard band [c2_in,
+// c2_out] (the FP32 sum starts from -mid, so this costs nothing): x <= hw is
+// the support cut and |x| <= hw finds the pairs inside the band.  With
+// c2 = x + mid the series exponent (Eq. 3 with d^2 = c2 (1 + c2 / 12))
+//   q1 c2 + q2 c2^2 + log2 omega = x (q1x + q2 x) + (log2 omega + e_mid)
+// with q1x = q1 + 2 q2 mid, e_mid = q1 mid + q2 mid^2; the producers store
+// log2 omega + e_mid with each candidate (e_mid = 0 for the other forms).
 struct PairConst {
-  float q1, q2, q4;          // exponent coefficients (log2 e folded in)
-  float c2_in, c2_out;       // guard band of the support cut (chord^2)
-  float c2_mid, c2_half;     // band test: |c2 - mid| <= half
+  float2 nmid;               // (-mid, -mid)
+  float2 q1x, q2;            // series form, both lanes
+  float2 q1, q4;             // exponent coefficients (log2 e folded in)
+  float2 mid2;               // (mid, mid)
+  float mid, hw;             // band centre and half-width (chord^2)
+  float e_mid;
 };
 
-// N weights omega w(p, k) of this thread's target against candidates cand[0
-// .. N-1] (tile-relative vectors, w = log2 omega) into w[], zero beyond the
-// support; pairs whose cut falls inside the guard band are decided from the
-// FP64 coordinates.  np counts the pairs with d <= r.
+template <int KT, bool BIG>
+__device__ __forceinline__ PairConst make_pair_const(const KernelDev& kd) {
+  PairConst P;
+  const float mid = 0.5f * (kd.c2_in + kd.c2_out);
+  P.mid = mid;
+  P.hw = 0.5f * (kd.c2_out - kd.c2_in);     // exact: the two are within 2x
+  P.nmid = make_float2(-mid, -mid);
+  P.mid2 = make_float2(mid, mid);
+  const double q1 = kd.k1, q2 = (double)kd.k1 / 12.0, m = mid;
+  const bool series = KT == CG_GAUSS1D && !BIG;
+  const float q1x = series ? (float)(q1 + 2.0 * q2 * m) : kd.k1;
+  P.q1x = make_float2(q1x, q1x);
+  P.q2 = make_float2((float)q2, (float)q2);
+  P.q1 = make_float2(kd.k1, kd.k1);
+  P.q4 = make_float2(kd.k2, kd.k2);
+  P.e_mid = series ? (float)(q1 * m + q2 * m * m) : 0.f;
+  return P;
+}
+
+// Per-target constants: the negated tile-relative vector and (elliptical
+// form) the major / minor axis directions, each duplicated for both lanes of
+// a packed pair.
+struct TgtConst {
+  float2 nx, ny, nz;
+  float2 f1x, f1y, f1z, f2x, f2y, f2z;
+};
+
+// x = c2 - mid of one candidate of a pair block, in the same operation order
+// as the packed evaluation (so both give the same bits).
+__device__ __forceinline__ float pair_x(const float* blk, int h, const TgtConst& T, float nmid) {
+  const float dx = blk[h] + T.nx.x, dy = blk[2 + h] + T.ny.x, dz = blk[4 + h] + T.nz.x;
+  return fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, nmid)));
+}
+
+// Candidates 0 .. n-1 of a group whose x lies in the guard band: the support
+// cut is decided from the FP64 coordinates.  Returns the mask of those that
+// lie outside the support after all.  Rare; kept out of line so that the
+// common path does not carry its registers.
+__device__ __noinline__ uint32_t band_fixup(const float* cand, const uint32_t* cidx, int n,
+                                            TgtConst T, float nmid, float hw,
+                                            const double2* tll, const double2* sll,
+                                            int64_t slot, double r_rad) {
+  uint32_t kill = 0;
+  for (int k = 0; k < n; ++k) {
+    const float x = pair_x(cand + 8 * (k >> 1), k & 1, T, nmid);
+    if (fabsf(x) <= hw) {
+      const double2 tl = tll[slot];
+      const double2 sl = sll[cidx[k]];
+      if (!(haversine_f64(tl.x, tl.y, sl.x, sl.y) <= r_rad)) kill |= 1u << k;
+    }
+  }
+  return kill;
+}
+
+// N weights omega w(p, k) of this thread's target against the candidates of
+// one group (N / 2 pair blocks) into w[], zero beyond the support; np counts
+// the pairs with d <= r.
 template <int N, int KT, bool BIG>
-__device__ __forceinline__ void eval_pairs(const float4* cand, const uint32_t* cidx, float4 at,
-                                           float4 f1, float4 f2, const PairConst& P,
+__device__ __forceinline__ void eval_group(const float* cand, const uint32_t* cidx,
+                                           const TgtConst& T, const PairConst& P,
                                            const TcArgs& a, int64_t slot, float* w,
                                            unsigned& np) {
-  float bm = INFINITY;     // distance of the nearest c2 to the band centre
+  float bm = INFINITY;     // smallest |x| of this thread's pairs
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const float4 cb = cand[k];
-    const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
-    const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float e;
+  for (int j = 0; j < N / 2; ++j) {
+    const float4 xy = *reinterpret_cast<const float4*>(cand + 8 * j);
+    const float4 zl = *reinterpret_cast<const float4*>(cand + 8 * j + 4);
+    const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), T.nx);
+    const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), T.ny);
+    const float2 dz = __fadd2_rn(make_float2(zl.x, zl.y), T.nz);
+    const float2 x = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, P.nmid)));
+    const float2 lw = make_float2(zl.z, zl.w);
+    float2 e;
     if (BIG) {
-      const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
-      const float d2 = d * d;
+      const float2 c2 = __fadd2_rn(x, P.mid2);
+      const float d0 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2.x)));
+      const float d1 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2.y)));
+      const float2 d2 = make_float2(d0 * d0, d1 * d1);
       if (KT == CG_GAUSS1D) {
-        e = fmaf(P.q1, d2, cb.w);
+        e = __ffma2_rn(P.q1, d2, lw);
       } else {
-        const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-        const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-        const float s2 = fmaf(ap, ap, bp * bp);
-        const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
-        e = fmaf(fmaf(P.q1 * ap, ap, P.q4 * bp * bp), ratio, cb.w);
+        const float2 ap = __ffma2_rn(dx, T.f1x, __ffma2_rn(dy, T.f1y, __fmul2_rn(dz, T.f1z)));
+        const float2 bp = __ffma2_rn(dx, T.f2x, __ffma2_rn(dy, T.f2y, __fmul2_rn(dz, T.f2z)));
+        const float2 s2 = __ffma2_rn(ap, ap, __fmul2_rn(bp, bp));
+        const float2 ratio = make_float2((s2.x > 0.f) ? __fdividef(d2.x, s2.x) : 1.f,
+                                         (s2.y > 0.f) ? __fdividef(d2.y, s2.y) : 1.f);
+        const float2 t = __ffma2_rn(__fmul2_rn(P.q1, ap), ap, __fmul2_rn(__fmul2_rn(P.q4, bp), bp));
+        e = __ffma2_rn(t, ratio, lw);
       }
     } else if (KT == CG_GAUSS1D) {
-      // d^2 = c^2 (1 + c^2/12) (the c^4/90 term is below FP32 here), folded
-      // into the exponent, plus log2(omega)
-      e = fmaf(c2, fmaf(c2, P.q2, P.q1), cb.w);
+      e = __ffma2_rn(x, __ffma2_rn(x, P.q2, P.q1x), lw);
     } else {
       // (d / sin d)^2 = 1 + c^2/3 + 17 c^4/180 (+ O(c^6))
-      const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
-      const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
-      const float ratio = fmaf(c2, fmaf(c2, 17.f / 180.f, 1.f / 3.f), 1.f);
-      e = fmaf(fmaf(P.q1 * ap, ap, P.q4 * bp * bp), ratio, cb.w);
+      const float2 c2 = __fadd2_rn(x, P.mid2);
+      const float2 ap = __ffma2_rn(dx, T.f1x, __ffma2_rn(dy, T.f1y, __fmul2_rn(dz, T.f1z)));
+      const float2 bp = __ffma2_rn(dx, T.f2x, __ffma2_rn(dy, T.f2y, __fmul2_rn(dz, T.f2z)));
+      const float2 ratio = __ffma2_rn(c2, __ffma2_rn(c2, make_float2(17.f / 180.f, 17.f / 180.f),
+                                                     make_float2(1.f / 3.f, 1.f / 3.f)),
+                                      make_float2(1.f, 1.f));
+      const float2 t = __ffma2_rn(__fmul2_rn(P.q1, ap), ap, __fmul2_rn(__fmul2_rn(P.q4, bp), bp));
+      e = __ffma2_rn(t, ratio, lw);
     }
-    const float wk = ex2_approx(e);
-    const bool in = c2 <= P.c2_out;
-    w[k] = in ? wk : 0.f;
-    np += in ? 1u : 0u;
-    bm = fminf(bm, fabsf(c2 - P.c2_mid));
+    const bool in0 = x.x <= P.hw, in1 = x.y <= P.hw;
+    w[2 * j] = in0 ? ex2_approx(e.x) : 0.f;
+    w[2 * j + 1] = in1 ? ex2_approx(e.y) : 0.f;
+    np += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+    bm = fminf(bm, fminf(fabsf(x.x), fabsf(x.y)));
   }
-  // rare: decide pairs inside the guard band from the FP64 coordinates
-  if (__any_sync(0xffffffffu, bm <= P.c2_half)) {
+  // rare: pairs inside the guard band are decided from the FP64 coordinates
+  if (bm <= P.hw) {
+    const uint32_t kill = band_fixup(cand, cidx, N, T, P.nmid.x, P.hw, a.tll, a.sll, slot,
+                                     a.kd.r_rad);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const float4 cb = cand[k];   // recomputed: cheaper than keeping N values live
-      const float dx = at.x - cb.x, dy = at.y - cb.y, dz = at.z - cb.z;
-      const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (c2 >= P.c2_in && c2 <= P.c2_out) {
-        const uint32_t idx = cidx[k];
-        const double2 tl = a.tll[slot];
-        const double2 sl = a.sll[idx];
-        const double d = haversine_f64(tl.x, tl.y, sl.x, sl.y);
-        if (!(d <= a.kd.r_rad)) {
-          w[k] = 0.f;
-          --np;
-        }
+    for (int k = 0; k < N; ++k)
+      if (kill & (1u << k)) {
+        w[k] = 0.f;
+        --np;
       }
-    }
   }
 }
 
@@ -369,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     uint8_t* p = smem_raw;
     S.B = p;
     p += (size_t)ns * cp * 64;
-    S.cand = reinterpret_cast<float4*>(p);
-    p += (size_t)ns * kK * sizeof(float4);
+    S.cand = reinterpret_cast<float*>(p);
+    p += (size_t)ns * kK * 4 * sizeof(float);
     S.reach = reinterpret_cast<float*>(p);
     p += (size_t)ns * 4 * kK * sizeof(float);
     S.cidx = reinterpret_cast<uint32_t*>(p);
@@ -429,16 +513,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (warp >= kProdWarp && warp < kProdWarp + kNP) {
     // ------------------------------------------------------------ producers
     const int pw = warp - kProdWarp;
+    const float e_mid = make_pair_const<KT, BIG>(a.kd).e_mid;
     const int nblk = cp / 64;                     // 64-channel blocks of a slab
     const uint32_t bytes = (uint32_t)kK * (uint32_t)cp * 2u;
-    int64_t item = blockIdx.x;
+    int64_t k = 0;
+    int64_t item = item_at(a, n_items, 0);
     int ch = 0;
-    int nch = (item < n_items) ? chunks_of(a, item) : 0;
-    advance(a, n_items, item, ch, nch, pw);
+    int nch = (item >= 0) ? chunks_of(a, item) : 0;
+    advance(a, n_items, k, item, ch, nch, pw);
     uint32_t q = (uint32_t)pw;
     Fetch f;
-    if (item < n_items) fetch_chunk(a, item, ch, lane, f);
-    while (item < n_items && !*abort_flag) {
+    if (item >= 0) fetch_chunk(a, item, ch, lane, f);
+    while (item >= 0 && !*abort_flag) {
       const int st = (int)(q % (uint32_t)kNS);
       if (q >= (uint32_t)kNS &&
           !mbar_wait(&S.empty[st], ((q / kNS) - 1) & 1, abort_flag)) {
@@ -456,7 +542,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
                          df_diff(f.h.z, f.l.z, f.chi.z, f.clo.z),
                          (w > 0.f) ? log2f(w) : -INFINITY);
       }
-      S.cand[st * kK + lane] = cb;
+      {
+        // pair-major: candidates 2j, 2j + 1 share the block j of 8 floats
+        float* blk = S.cand + (size_t)st * kK * 4 + 8 * (lane >> 1) + (lane & 1);
+        blk[0] = cb.x;
+        blk[2] = cb.y;
+        blk[4] = cb.z;
+        blk[6] = cb.w + e_mid;
+      }
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
         const float ex = cb.x - f.sq[qq].x, ey = cb.y - f.sq[qq].y, ez = cb.z - f.sq[qq].z;
@@ -494,9 +587,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
       }
       // next own chunk: issue its loads now, consume them after the next wait
-      advance(a, n_items, item, ch, nch, kNP);
+      advance(a, n_items, k, item, ch, nch, kNP);
       q += kNP;
-      if (item < n_items) fetch_chunk(a, item, ch, lane, f);
+      if (item >= 0) fetch_chunk(a, item, ch, lane, f);
     }
   } else if (warp >= kEpiWarp && warp < kEpiWarp + kEW) {
     // ------------------------------------------------------------ epilogue
@@ -508,7 +601,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     constexpr int kGroups = kWW / 4;
     uint32_t tq = 0;
-    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+    for (int64_t item = item_at(a, n_items, 0); item >= 0 && !*abort_flag;
+         item = item_at(a, n_items, (int64_t)tq + 1), ++tq) {
       const int64_t tile = item / a.n_slabs;
       const int slab = (int)(item % a.n_slabs);
       const int c_base = slab * cp;
@@ -624,7 +718,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       uint32_t q = 0, tq = 0;
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
                              ((uint32_t)(cp >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
-      for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+      for (int64_t item = item_at(a, n_items, 0); item >= 0 && !*abort_flag;
+           item = item_at(a, n_items, (int64_t)tq + 1), ++tq) {
         const int nch = chunks_of(a, item);
         if (tq > 0 && !mbar_wait(S.dempty, (tq - 1) & 1, abort_flag)) {
           set_error(a.err, ERR_TIMEOUT);
@@ -687,31 +782,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int grp = warp >> 2;                // candidates 16 grp .. 16 grp + 15
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const float rc = sqrtf(a.kd.c2_out);      // support radius as a chord
-    PairConst P;
-    P.q1 = a.kd.k1;
-    P.q2 = a.kd.k1 * (1.f / 12.f);
-    P.q4 = a.kd.k2;
-    P.c2_in = a.kd.c2_in;
-    P.c2_out = a.kd.c2_out;
-    // pre-test for the guard band: |c2 - mid| <= half must hold for every c2
-    // in [c2_in, c2_out].  The band is only ~240 FP32 ulps wide, and mid and
-    // the difference are rounded, so the half-width gets 10% (~24 ulps) of
-    // slack; the exact test inside decides.
-    P.c2_mid = 0.5f * (P.c2_in + P.c2_out);
-    P.c2_half = 0.5f * (P.c2_out - P.c2_in) * 1.1f + 1e-30f;
+    const PairConst P = make_pair_const<KT, BIG>(a.kd);
     uint32_t q = 0, tq = 0;
     unsigned npair = 0;
-    for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x, ++tq) {
+    for (int64_t item = item_at(a, n_items, 0); item >= 0 && !*abort_flag;
+         item = item_at(a, n_items, (int64_t)tq + 1), ++tq) {
       const int64_t tile = item / a.n_slabs;
       const int slab = (int)(item % a.n_slabs);
-      const int c_base = slab * cp;
       const int64_t slot = tile * kT + row;
       if (slot >= a.n_slots) set_error(a.err, ERR_INTERNAL);
-      const float4 at = a.ta[slot];
-      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
-      if (KT == CG_GAUSS2D) {
-        f1 = a.f1[slot];
-        f2 = a.f2[slot];
+      TgtConst T;
+      {
+        const float4 at = a.ta[slot];
+        T.nx = make_float2(-at.x, -at.x);
+        T.ny = make_float2(-at.y, -at.y);
+        T.nz = make_float2(-at.z, -at.z);
+        float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
+        if (KT == CG_GAUSS2D) {
+          f1 = a.f1[slot];
+          f2 = a.f2[slot];
+        }
+        T.f1x = make_float2(f1.x, f1.x);
+        T.f1y = make_float2(f1.y, f1.y);
+        T.f1z = make_float2(f1.z, f1.z);
+        T.f2x = make_float2(f2.x, f2.x);
+        T.f2y = make_float2(f2.y, f2.y);
+        T.f2z = make_float2(f2.z, f2.z);
       }
       const int nch = chunks_of(a, item);
       // the quarter's reach: candidates beyond (quarter radius + r) give w = 0
@@ -736,24 +832,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         float w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0.f;
+        const float* cg = S.cand + (size_t)kb * 4;
         if (live & 0xffu)
-          eval_pairs<8, KT, BIG>(S.cand + kb, S.cidx + kb, at, f1, f2, P, a, slot, w, np_item);
+          eval_group<8, KT, BIG>(cg, S.cidx + kb, T, P, a, slot, w, np_item);
         if (live & 0xff00u)
-          eval_pairs<8, KT, BIG>(S.cand + kb + 8, S.cidx + kb + 8, at, f1, f2, P, a, slot, w + 8,
-                                 np_item);
+          eval_group<8, KT, BIG>(cg + 32, S.cidx + kb + 8, T, P, a, slot, w + 8, np_item);
         uint32_t packed[8], packed_lo[8];
-        float part = 0.f;
+        float2 part2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          part += w[2 * j] + w[2 * j + 1];
+          const float2 wp = make_float2(w[2 * j], w[2 * j + 1]);
+          part2 = __fadd2_rn(part2, wp);
           if (SPLIT) {
             // w = w_hi + w_lo: w_hi keeps the top 8 significand bits (exact
             // truncation), w_lo = w - w_hi is exact in FP32, then rounded
-            const uint32_t u0 = __float_as_uint(w[2 * j]) & 0xffff0000u;
-            const uint32_t u1 = __float_as_uint(w[2 * j + 1]) & 0xffff0000u;
+            const uint32_t u0 = __float_as_uint(wp.x), u1 = __float_as_uint(wp.y);
             packed[j] = __byte_perm(u0, u1, 0x7632);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(w[2 * j] - __uint_as_float(u0),
-                                                            w[2 * j + 1] - __uint_as_float(u1));
+            const float2 hi = make_float2(__uint_as_float(u0 & 0xffff0000u),
+                                          __uint_as_float(u1 & 0xffff0000u));
+            const float2 lo = __ffma2_rn(hi, make_float2(-1.f, -1.f), wp);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(lo.x, lo.y);
             packed_lo[j] = *reinterpret_cast<const uint32_t*>(&l2);
           } else {
             const __nv_bfloat162 b2 = __floats2bfloat162_rn(w[2 * j], w[2 * j + 1]);
@@ -763,7 +861,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         // Kahan accumulation of the chunk partial into the weight map
         {
-          const float y = part - wc;
+          const float y = (part2.x + part2.y) - wc;
           const float t = ws + y;
           wc = (t - ws) - y;
           ws = t;
@@ -819,6 +917,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(a.tmem_cols));
+  }
+}
+
+// Items ranked by decreasing cost for the persistent schedule (item_at):
+// cost = the tile's chunks + 8 (the epilogue's share of an item), clamped to
+// kOrderBins - 1; one CTA counting-sorts the items on it.  Items of equal cost
+// take their ranks in any order (the assignment does not change any result:
+// every item is computed whole by one CTA).
+constexpr int kOrderBins = 4096;
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ int order_bin(int32_t cand) {
+  const int c = (cand + kK - 1) / kK + 8;
+  return kOrderBins - 1 - min(c, kOrderBins - 1);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_item_order(const int32_t* __restrict__ tile_cand,
+                                                              int n_slabs, int64_t n_items,
+                                                              int32_t* __restrict__ order) {
+  __shared__ int32_t cnt[kOrderBins];
+  __shared__ int32_t wsum[kOrderThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < kOrderBins; i += kOrderThreads) cnt[i] = 0;
+  __syncthreads();
+  for (int64_t it = tid; it < n_items; it += kOrderThreads)
+    atomicAdd(&cnt[order_bin(tile_cand[it / n_slabs])], 1);
+  __syncthreads();
+  // exclusive scan of the bins: thread t owns bins 4 t .. 4 t + 3
+  constexpr int kPer = kOrderBins / kOrderThreads;
+  int v[kPer], sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = cnt[kPer * tid + j];
+    sum += v[j];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  int base = incl - sum + (warp > 0 ? wsum[warp - 1] : 0);
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    cnt[kPer * tid + j] = base;
+    base += v[j];
+  }
+  __syncthreads();
+  for (int64_t it = tid; it < n_items; it += kOrderThreads) {
+    const int pos = atomicAdd(&cnt[order_bin(tile_cand[it / n_slabs])], 1);
+    order[pos] = (int32_t)it;
   }
 }
 
@@ -922,6 +1083,22 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, fl
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) return cudaSuccess;
+  // balanced persistent schedule: with several items per CTA, rank the items
+  // by cost so that the CTAs' totals match (tiles differ in candidates)
+  a.order = nullptr;
+  if (items > grid && items <= INT32_MAX) {
+    Tiling& tw = g->t128;
+    if (tw.cap_order < items) {
+      dfree(tw.order, g->stream);
+      tw.cap_order = 0;
+      cudaError_t ea = dalloc(&tw.order, (size_t)items, g->stream);
+      if (ea != cudaSuccess) return ea;
+      tw.cap_order = items;
+    }
+    k_item_order<<<1, kOrderThreads, 0, g->stream>>>(t.tile_cand, a.n_slabs, items, tw.order);
+    g->n_launches += 1;
+    a.order = tw.order;
+  }
   // tensor map over the caller's [N][C] BF16 rows: 64-channel x 1-row boxes,
   // 128-byte swizzle (the layout of the MMA's B operand); rows past N read 0
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();

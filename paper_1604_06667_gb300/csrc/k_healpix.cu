@@ -257,6 +257,8 @@ void tiling_free(Tiling& t, cudaStream_t s) {
   dfree(t.c64, s);
   dfree(t.a, s);
   dfree(t.tile_cand, s);
+  dfree(t.order, s);
+  t.cap_order = 0;
   dfree(t.sub64, s);
   dfree(t.subf, s);
   dfree(t.range_off, s);

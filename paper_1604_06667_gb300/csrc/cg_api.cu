@@ -348,6 +348,12 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
   const double r = support_deg * kDeg2Rad;
   const double chord = 2.0 * std::sin(0.5 * std::fmin(r, kPi));
   kd.r_rad = r;
+  {
+    const double c2r = chord * chord;
+    kd.c2r_hi = (float)c2r;
+    kd.c2r_lo = (float)(c2r - (double)kd.c2r_hi);
+    kd.c2r_tol = (float)(1e-9 * c2r + 1e-12 * chord);
+  }
   kd.c2_cut = (float)(chord * chord);
   kd.c2_in = (float)(chord * chord * (1.0 - 1e-5));
   kd.c2_out = (float)(chord * chord * (1.0 + 1e-5));

@@ -35,6 +35,8 @@ struct KernelDev {        // kernel constants used by the gridder
   float c2_in, c2_out;    // chord^2 below c2_in: inside; above c2_out: outside
   float c2_cut;           // chord^2 of the support radius
   double r_rad;           // support radius (FP64 guard-band decision)
+  float c2r_hi, c2r_lo;   // FP64 squared chord of r as a double-float pair
+  float c2r_tol;          // tolerance of the double-float squared chord of a pair
   int big_support;        // 1 if the chord series for d^2 is not accurate enough
   float dscale;           // 0; else the weight is w d^2 dscale (d/dsigma pass)
 };

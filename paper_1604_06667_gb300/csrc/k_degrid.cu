@@ -24,6 +24,7 @@
 // epilogue that forms dR and, given an upstream gradient g, the scalar
 // sum_pc g_pc dR_pc with a deterministic two-level FP64 reduction.
 #include "cg_common.cuh"
+#include "cg_cut.cuh"
 #include "cg_healpix.cuh"
 #include "cg_internal.h"
 #include "cg_trig.cuh"
@@ -79,16 +80,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-__device__ __noinline__ double haversine_f64(double l1, double b1, double l2, double b2) {
-  const double p1 = b1 * kDeg2Rad, p2 = b2 * kDeg2Rad;
-  const double dl = (l2 - l1) * kDeg2Rad;
-  const double sdp = sin(0.5 * (p2 - p1));
-  const double sdl = sin(0.5 * dl);
-  double h = sdp * sdp + cos(p1) * cos(p2) * sdl * sdl;
-  h = fmin(h, 1.0);
-  return 2.0 * asin(sqrt(h));
 }
 
 struct DegridArgs {
@@ -243,9 +234,9 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
               }
               coef = ex2_approx(ex) * h.w * iw;
               if (c2 >= a.kd.c2_in) {
-                const double2 tg = a.tll[slot];
-                const double d = haversine_f64(tg.x, tg.y, sll.x, sll.y);
-                if (!(d <= a.kd.r_rad)) coef = 0.f;
+                if (!pair_inside(a.tll[slot], sll, a.kd.c2r_hi, a.kd.c2r_lo, a.kd.c2r_tol,
+                                 a.kd.r_rad))
+                  coef = 0.f;
               }
             }
             if (!__any_sync(0xffffffffu, coef != 0.f)) continue;

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "cg_common.cuh"
+#include "cg_cut.cuh"
 #include "cg_internal.h"
 
 namespace cg {
@@ -62,17 +63,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// Great-circle distance by the Haversine formula in FP64 (guard band only).
-__device__ __noinline__ double haversine_f64(double l1, double b1, double l2, double b2) {
-  const double p1 = b1 * kDeg2Rad, p2 = b2 * kDeg2Rad;
-  const double dl = (l2 - l1) * kDeg2Rad;
-  const double sdp = sin(0.5 * (p2 - p1));
-  const double sdl = sin(0.5 * dl);
-  double h = sdp * sdp + cos(p1) * cos(p2) * sdl * sdl;
-  h = fmin(h, 1.0);
-  return 2.0 * asin(sqrt(h));
 }
 
 template <typename DT>
@@ -267,12 +257,11 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
           w = ex2_approx(ex) * sh.w;
           if (a.kd.dscale != 0.f) w *= d2 * a.kd.dscale;   // dw/dsigma pass
           if (c2 >= a.kd.c2_in) {
-            // guard band: decide d <= r in FP64 from the input coordinates
+            // guard band: decide d <= r again from the input coordinates
             const uint32_t idx = sh_idx[k];
-            const double2 tl = a.tgt_ll[slot];
-            const double2 sl = a.sll[idx];
-            const double d = haversine_f64(tl.x, tl.y, sl.x, sl.y);
-            if (!(d <= a.kd.r_rad)) w = -1.f;
+            if (!pair_inside(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo, a.kd.c2r_tol,
+                             a.kd.r_rad))
+              w = -1.f;
           }
           if (w >= 0.f) ++npair; else w = 0.f;
         }

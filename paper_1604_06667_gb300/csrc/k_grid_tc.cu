@@ -51,6 +51,7 @@
 #include <cmath>
 
 #include "cg_common.cuh"
+#include "cg_cut.cuh"
 #include "cg_internal.h"
 
 namespace cg {
@@ -181,16 +182,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-__device__ __noinline__ double haversine_f64(double l1, double b1, double l2, double b2) {
-  const double p1 = b1 * kDeg2Rad, p2 = b2 * kDeg2Rad;
-  const double dl = (l2 - l1) * kDeg2Rad;
-  const double sdp = sin(0.5 * (p2 - p1));
-  const double sdl = sin(0.5 * dl);
-  double h = sdp * sdp + cos(p1) * cos(p2) * sdl * sdl;
-  h = fmin(h, 1.0);
-  return 2.0 * asin(sqrt(h));
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -356,21 +347,19 @@ __device__ __forceinline__ float pair_x(const float* blk, int h, const TgtConst&
 }
 
 // Candidates 0 .. n-1 of a group whose x lies in the guard band: the support
-// cut is decided from the FP64 coordinates.  Returns the mask of those that
-// lie outside the support after all.  Rare; kept out of line so that the
-// common path does not carry its registers.
+// cut is decided again from the input coordinates (pair_inside).  Returns the
+// mask of those that lie outside the support after all.  Rare; kept out of
+// line so that the common path does not carry its registers.
 __device__ __noinline__ uint32_t band_fixup(const float* cand, const uint32_t* cidx, int n,
                                             TgtConst T, float nmid, float hw,
                                             const double2* tll, const double2* sll,
-                                            int64_t slot, double r_rad) {
+                                            int64_t slot, const KernelDev& kd) {
   uint32_t kill = 0;
   for (int k = 0; k < n; ++k) {
     const float x = pair_x(cand + 8 * (k >> 1), k & 1, T, nmid);
-    if (fabsf(x) <= hw) {
-      const double2 tl = tll[slot];
-      const double2 sl = sll[cidx[k]];
-      if (!(haversine_f64(tl.x, tl.y, sl.x, sl.y) <= r_rad)) kill |= 1u << k;
-    }
+    if (fabsf(x) <= hw &&
+        !pair_inside(tll[slot], sll[cidx[k]], kd.c2r_hi, kd.c2r_lo, kd.c2r_tol, kd.r_rad))
+      kill |= 1u << k;
   }
   return kill;
 }
@@ -431,8 +420,7 @@ __device__ __forceinline__ void eval_group(const float* cand, const uint32_t* ci
   }
   // rare: pairs inside the guard band are decided from the FP64 coordinates
   if (bm <= P.hw) {
-    const uint32_t kill = band_fixup(cand, cidx, N, T, P.nmid.x, P.hw, a.tll, a.sll, slot,
-                                     a.kd.r_rad);
+    const uint32_t kill = band_fixup(cand, cidx, N, T, P.nmid.x, P.hw, a.tll, a.sll, slot, a.kd);
 #pragma unroll
     for (int k = 0; k < N; ++k)
       if (kill & (1u << k)) {

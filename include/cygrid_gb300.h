@@ -144,6 +144,32 @@ cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_d
                           int64_t n_samples, float* out, int32_t layout_channel_major,
                           float* out_weights);
 
+/* One-shot gridding of samples held in HOST memory: the end-to-end form of
+ * cg_grid_oneshot.  The call copies the coordinates, channel data and
+ * weights into device staging buffers owned by the handle, grids them exactly
+ * as cg_grid_oneshot does, and copies the map (and weight map) back into the
+ * caller's host arrays.
+ *   h_lon, h_lat, h_data, h_weights   host arrays with the shapes and types of
+ *                        cg_grid_oneshot's device arguments (h_weights may be
+ *                        NULL); page-locked memory (cudaHostAlloc or
+ *                        cudaHostRegister) lets the copies run asynchronously,
+ *                        pageable memory makes them synchronous.
+ *   h_out                host float32 [n_targets][C] (layout 0) or
+ *                        [C][n_targets] (layout 1).
+ *   h_out_weights        host float32 [n_targets] (W_p), or NULL.
+ * Asynchronous: every host array must stay valid and unmodified until
+ * cg_sync returns, which also reports device errors.  Consecutive calls on
+ * one handle are pipelined over two staging slots: call k + 1 copies its
+ * inputs on a copy-in stream while call k computes on the handle's stream and
+ * the map of call k - 1 is copied back on a copy-out stream; within a call
+ * the sample index is built while the channel data are still being copied.
+ * Device memory: two slots of N (20 + C b) + P (C + 1) 4 bytes (b = 2 for
+ * BF16, 4 for F32), grown on demand and kept until cg_grid_destroy. */
+cg_status cg_grid_oneshot_host(cg_grid* g, const double* h_lon, const double* h_lat,
+                               const void* h_data, int32_t data_dtype, const float* h_weights,
+                               int64_t n_samples, float* h_out, int32_t layout_channel_major,
+                               float* h_out_weights);
+
 /* Zero the accumulators (asynchronous). */
 cg_status cg_grid_reset(cg_grid* g);
 
@@ -156,7 +182,8 @@ cg_status cg_set_stream(cg_grid* g, void* stream);
 /* Select the channel-accumulation form (cg_path). */
 cg_status cg_set_path(cg_grid* g, int32_t path);
 
-/* Wait for the handle's stream and report device-side errors. */
+/* Wait for the handle's stream (and the copy streams of
+ * cg_grid_oneshot_host) and report device-side errors. */
 cg_status cg_sync(cg_grid* g);
 
 /* Thread-local description of the last error ("" if none). */

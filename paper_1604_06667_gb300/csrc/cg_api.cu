@@ -220,6 +220,8 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
     t.ranges_gen = g->index_gen;
   }
   cudaEvent_t t3 = tmark(g);
+  // host-buffer calls: the index is built while the channel data still copy
+  if (g->data_ready) CG_CUDA(cudaStreamWaitEvent(g->stream, g->data_ready, 0), where);
   if (tc) {
     const bool fuse = out != nullptr && g->acc_empty;
     const int mode = fuse ? 2 : (g->acc_empty ? 0 : 1);
@@ -237,6 +239,48 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
   g->total_n += n;
   if (!(fused && *fused)) g->acc_empty = false;
   return CG_OK;
+}
+
+// Reset, add, finalize (the body of the one-shot calls).
+cg_status oneshot_impl(cg_grid* g, const double* lon, const double* lat, const void* data,
+                       int32_t dtype, const float* weights, int64_t n, float* out,
+                       int32_t layout_channel_major, float* out_w, const char* where) {
+  cg_status st = zero_acc(g);
+  if (st != CG_OK) return st;
+  bool fused = false;
+  st = do_add(g, lon, lat, data, dtype, weights, n, where, layout_channel_major ? nullptr : out,
+              out_w, &fused);
+  if (st != CG_OK) return st;
+  if (fused) return CG_OK;  // the tensor-core epilogue already wrote Eq. 3
+  st = clear_if_empty(g, where);
+  if (st != CG_OK) return st;
+  cudaEvent_t t0 = tmark(g);
+  CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_w), where);
+  tstage(g, 4, t0, tmark(g));
+  return CG_OK;
+}
+
+void free_pipe(cg_grid* g) {
+  HostPipe* p = g->pipe;
+  if (!p) return;
+  if (p->s_in) cudaStreamSynchronize(p->s_in);
+  if (p->s_out) cudaStreamSynchronize(p->s_out);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(p->lon[i]);
+    cudaFree(p->lat[i]);
+    cudaFree(p->data[i]);
+    cudaFree(p->weights[i]);
+    cudaFree(p->out[i]);
+    cudaFree(p->out_w[i]);
+    if (p->coords[i]) cudaEventDestroy(p->coords[i]);
+    if (p->in_done[i]) cudaEventDestroy(p->in_done[i]);
+    if (p->comp_done[i]) cudaEventDestroy(p->comp_done[i]);
+    if (p->out_done[i]) cudaEventDestroy(p->out_done[i]);
+  }
+  if (p->s_in) cudaStreamDestroy(p->s_in);
+  if (p->s_out) cudaStreamDestroy(p->s_out);
+  delete p;
+  g->pipe = nullptr;
 }
 
 }  // namespace
@@ -402,18 +446,111 @@ cg_status cg_grid_oneshot(cg_grid* g, const double* lon_deg, const double* lat_d
   if (!out) return fail(CG_EINVAL, "cg_grid_oneshot: out is null");
   if (!g->kernel_set) return fail(CG_ESTATE, "cg_grid_oneshot: call cg_set_kernel first");
   CG_CUDA(cudaSetDevice(g->device), "cg_grid_oneshot");
-  cg_status st = zero_acc(g);
+  return oneshot_impl(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, out,
+                      layout_channel_major, out_weights, "cg_grid_oneshot");
+}
+
+cg_status cg_grid_oneshot_host(cg_grid* g, const double* h_lon, const double* h_lat,
+                               const void* h_data, int32_t data_dtype, const float* h_weights,
+                               int64_t n_samples, float* h_out, int32_t layout_channel_major,
+                               float* h_out_weights) {
+  const char* where = "cg_grid_oneshot_host";
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (!h_lon || !h_lat || !h_data || !h_out)
+    return fail(CG_EINVAL, "%s: null coordinate, data or output pointer", where);
+  if (data_dtype != CG_F32 && data_dtype != CG_BF16)
+    return fail(CG_EINVAL, "%s: data_dtype must be CG_F32 or CG_BF16", where);
+  if (n_samples < 0 || n_samples > 0x7fffffffLL)
+    return fail(CG_EINVAL, "%s: n_samples out of range", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  if (!g->pipe) {
+    HostPipe* p = new HostPipe();
+    g->pipe = p;
+    CG_CUDA(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking), where);
+    CG_CUDA(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking), where);
+    for (int i = 0; i < 2; ++i) {
+      CG_CUDA(cudaEventCreateWithFlags(&p->coords[i], cudaEventDisableTiming), where);
+      CG_CUDA(cudaEventCreateWithFlags(&p->in_done[i], cudaEventDisableTiming), where);
+      CG_CUDA(cudaEventCreateWithFlags(&p->comp_done[i], cudaEventDisableTiming), where);
+      CG_CUDA(cudaEventCreateWithFlags(&p->out_done[i], cudaEventDisableTiming), where);
+    }
+  }
+  HostPipe* p = g->pipe;
+  const int s = p->next;
+  p->next ^= 1;
+  const size_t n = (size_t)n_samples;
+  const size_t dbytes = n * (size_t)g->C * (data_dtype == CG_BF16 ? 2 : 4);
+  const size_t obytes = (size_t)g->P * (size_t)g->C * sizeof(float);
+  // (re)allocate this slot's staging once its previous use has drained
+  if (p->cap_n[s] < n || p->cap_data[s] < dbytes || !p->have_out[s] ||
+      (h_out_weights && !p->have_w[s])) {
+    if (p->used[s]) CG_CUDA(cudaEventSynchronize(p->out_done[s]), where);
+    if (p->cap_n[s] < n) {
+      cudaFree(p->lon[s]);
+      cudaFree(p->lat[s]);
+      cudaFree(p->weights[s]);
+      p->lon[s] = p->lat[s] = nullptr;
+      p->weights[s] = nullptr;
+      p->cap_n[s] = 0;
+      const size_t m = n > 0 ? n : 1;
+      CG_CUDA(cudaMalloc(&p->lon[s], m * sizeof(double)), where);
+      CG_CUDA(cudaMalloc(&p->lat[s], m * sizeof(double)), where);
+      CG_CUDA(cudaMalloc(&p->weights[s], m * sizeof(float)), where);
+      p->cap_n[s] = n;
+    }
+    if (p->cap_data[s] < dbytes) {
+      cudaFree(p->data[s]);
+      p->data[s] = nullptr;
+      p->cap_data[s] = 0;
+      CG_CUDA(cudaMalloc(&p->data[s], dbytes > 0 ? dbytes : 16), where);
+      p->cap_data[s] = dbytes;
+    }
+    if (!p->have_out[s]) {
+      CG_CUDA(cudaMalloc(&p->out[s], obytes > 0 ? obytes : 16), where);
+      p->have_out[s] = true;
+    }
+    if (h_out_weights && !p->have_w[s]) {
+      CG_CUDA(cudaMalloc(&p->out_w[s], (size_t)(g->P > 0 ? g->P : 1) * sizeof(float)), where);
+      p->have_w[s] = true;
+    }
+  }
+  // copy-in: after the compute that last read this slot's inputs
+  if (p->used[s]) CG_CUDA(cudaStreamWaitEvent(p->s_in, p->comp_done[s], 0), where);
+  CG_CUDA(cudaMemcpyAsync(p->lon[s], h_lon, n * sizeof(double), cudaMemcpyHostToDevice, p->s_in),
+          where);
+  CG_CUDA(cudaMemcpyAsync(p->lat[s], h_lat, n * sizeof(double), cudaMemcpyHostToDevice, p->s_in),
+          where);
+  if (h_weights)
+    CG_CUDA(cudaMemcpyAsync(p->weights[s], h_weights, n * sizeof(float), cudaMemcpyHostToDevice,
+                            p->s_in),
+            where);
+  CG_CUDA(cudaEventRecord(p->coords[s], p->s_in), where);
+  CG_CUDA(cudaMemcpyAsync(p->data[s], h_data, dbytes, cudaMemcpyHostToDevice, p->s_in), where);
+  CG_CUDA(cudaEventRecord(p->in_done[s], p->s_in), where);
+  // compute: the index waits for the coordinates only, the gridder for the
+  // data; the map buffer must have been copied out by this slot's last use
+  CG_CUDA(cudaStreamWaitEvent(g->stream, p->coords[s], 0), where);
+  if (p->used[s]) CG_CUDA(cudaStreamWaitEvent(g->stream, p->out_done[s], 0), where);
+  g->data_ready = p->in_done[s];
+  cg_status st = oneshot_impl(g, p->lon[s], p->lat[s], p->data[s], data_dtype,
+                              h_weights ? p->weights[s] : nullptr, n_samples, p->out[s],
+                              layout_channel_major, h_out_weights ? p->out_w[s] : nullptr, where);
+  g->data_ready = nullptr;
   if (st != CG_OK) return st;
-  bool fused = false;
-  st = do_add(g, lon_deg, lat_deg, data, data_dtype, weights, n_samples, "cg_grid_oneshot",
-              layout_channel_major ? nullptr : out, out_weights, &fused);
-  if (st != CG_OK) return st;
-  if (fused) return CG_OK;  // the tensor-core epilogue already wrote Eq. 3
-  st = clear_if_empty(g, "cg_grid_oneshot");
-  if (st != CG_OK) return st;
-  cudaEvent_t t0 = tmark(g);
-  CG_CUDA(finalize_maps(g, out, layout_channel_major ? 1 : 0, out_weights), "cg_grid_oneshot");
-  tstage(g, 4, t0, tmark(g));
+  // the gridder may have been skipped (no samples): order the data copy anyway
+  CG_CUDA(cudaStreamWaitEvent(g->stream, p->in_done[s], 0), where);
+  CG_CUDA(cudaEventRecord(p->comp_done[s], g->stream), where);
+  // copy-out
+  CG_CUDA(cudaStreamWaitEvent(p->s_out, p->comp_done[s], 0), where);
+  CG_CUDA(cudaMemcpyAsync(h_out, p->out[s], obytes, cudaMemcpyDeviceToHost, p->s_out), where);
+  if (h_out_weights)
+    CG_CUDA(cudaMemcpyAsync(h_out_weights, p->out_w[s], (size_t)g->P * sizeof(float),
+                            cudaMemcpyDeviceToHost, p->s_out),
+            where);
+  CG_CUDA(cudaEventRecord(p->out_done[s], p->s_out), where);
+  p->used[s] = true;
   return CG_OK;
 }
 
@@ -428,6 +565,7 @@ cg_status cg_grid_destroy(cg_grid* g) {
   g_last_error.clear();
   if (!g) return CG_OK;
   cudaSetDevice(g->device);
+  free_pipe(g);
   free_all(g);
   cudaError_t e = cudaStreamSynchronize(g->stream);
   delete g;
@@ -457,6 +595,10 @@ cg_status cg_sync(cg_grid* g) {
   g_last_error.clear();
   if (!g) return fail(CG_EINVAL, "cg_sync: null handle");
   CG_CUDA(cudaSetDevice(g->device), "cg_sync");
+  if (g->pipe) {
+    CG_CUDA(cudaStreamSynchronize(g->pipe->s_in), "cg_sync");
+    CG_CUDA(cudaStreamSynchronize(g->pipe->s_out), "cg_sync");
+  }
   return check_device(g, "cg_sync");
 }
 

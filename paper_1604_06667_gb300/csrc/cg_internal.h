@@ -80,9 +80,30 @@ struct SortWork {         // radix-sort scratch
 
 }  // namespace cg
 
+namespace cg {
+// Staging for cg_grid_oneshot_host: two slots of device buffers, a copy-in
+// and a copy-out stream, and the events that order the three streams.
+struct HostPipe {
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t coords[2] = {}, in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+  bool used[2] = {false, false};
+  double* lon[2] = {};
+  double* lat[2] = {};
+  void* data[2] = {};
+  float* weights[2] = {};
+  float* out[2] = {};
+  float* out_w[2] = {};
+  size_t cap_n[2] = {0, 0}, cap_data[2] = {0, 0};
+  bool have_out[2] = {false, false}, have_w[2] = {false, false};
+  int next = 0;
+};
+}  // namespace cg
+
 struct cg_grid {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cg::HostPipe* pipe = nullptr;   // cg_grid_oneshot_host staging (created on first use)
+  cudaEvent_t data_ready = nullptr;  // if set: the gridder waits for it (channel data copy)
   int64_t P = 0;
   int32_t C = 0;
   int32_t path = CG_PATH_AUTO;

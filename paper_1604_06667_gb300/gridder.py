@@ -130,6 +130,45 @@ class Gridder:
         self._keep = (lon, lat, data, weights)
         return out
 
+    def grid_oneshot_host(self, lon, lat, data, out, weights=None, out_weights=None,
+                          channel_major: bool = False):
+        """One-shot gridding of samples in host memory into the host array
+        ``out`` (cg_grid_oneshot_host): inputs are copied in, the map is
+        copied back.  CPU tensors, contiguous (page-locked ones let
+        consecutive calls overlap their copies with the computation); they
+        must stay alive and unmodified until ``sync()``."""
+        def host(t, dtype=None):
+            t = torch.as_tensor(t)
+            if t.device.type != "cpu":
+                raise ValueError("grid_oneshot_host takes host (CPU) tensors")
+            if dtype is not None and t.dtype != dtype:
+                raise ValueError("expected %s, got %s" % (dtype, t.dtype))
+            if not t.is_contiguous():
+                raise ValueError("host tensors must be contiguous")
+            return t
+        lon, lat = host(lon, torch.float64), host(lat, torch.float64)
+        data = host(data)
+        if data.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError("data must be float32 or bfloat16")
+        n = int(lon.numel())
+        if lat.numel() != n or data.numel() != n * self.n_channels:
+            raise ValueError("lon, lat and data disagree in the sample count")
+        out = host(out, torch.float32)
+        if out.numel() != self.n_targets * self.n_channels:
+            raise ValueError("out must hold n_targets x n_channels floats")
+        if weights is not None:
+            weights = host(weights, torch.float32)
+        if out_weights is not None:
+            out_weights = host(out_weights, torch.float32)
+        C.cg_grid_oneshot_host(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
+                               _ptr(weights), n, _ptr(out), 1 if channel_major else 0,
+                               _ptr(out_weights))
+        self._keep_host = getattr(self, "_keep_host", [])[-3:] + [(lon, lat, data, weights, out,
+                                                                    out_weights)]
+        self.index_gen = getattr(self, "index_gen", 0) + 1
+        self.n_samples = n
+        return out
+
     # -- adjoint and kernel-width derivative ------------------------------
     def degrid(self, ymap, map_weights=None, out=None):
         """G^T y: the adjoint of the normalised gridding of the last add's

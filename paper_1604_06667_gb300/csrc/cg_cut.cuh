@@ -44,8 +44,8 @@ __device__ __forceinline__ void df_unit_vector(double lon, double lat, df32& x, 
 // Is the pair (target (lon, lat) tl, sample sl, degrees) within the support?
 // c2r_hi + c2r_lo: FP64 squared chord of r as a double-float; c2r_tol: the
 // tolerance of the double-float squared chord (see above); r_rad: r.
-__device__ __noinline__ bool pair_inside(double2 tl, double2 sl, float c2r_hi, float c2r_lo,
-                                         float c2r_tol, double r_rad) {
+__device__ __forceinline__ bool pair_inside_inl(double2 tl, double2 sl, float c2r_hi,
+                                                float c2r_lo, float c2r_tol, double r_rad) {
   df32 tx, ty, tz, sx, sy, sz;
   df_unit_vector(tl.x, tl.y, tx, ty, tz);
   df_unit_vector(sl.x, sl.y, sx, sy, sz);
@@ -57,6 +57,13 @@ __device__ __noinline__ bool pair_inside(double2 tl, double2 sl, float c2r_hi, f
   if (diff.hi > c2r_tol) return false;
   if (diff.hi < -c2r_tol) return true;
   return cut_haversine_f64(tl.x, tl.y, sl.x, sl.y) <= r_rad;
+}
+
+// The same decision out of line (for call sites inside loops whose
+// registers it should not inflate).
+__device__ __noinline__ bool pair_inside(double2 tl, double2 sl, float c2r_hi, float c2r_lo,
+                                         float c2r_tol, double r_rad) {
+  return pair_inside_inl(tl, sl, c2r_hi, c2r_lo, c2r_tol, r_rad);
 }
 
 }  // namespace

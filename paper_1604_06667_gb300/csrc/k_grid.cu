@@ -259,8 +259,8 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
           if (c2 >= a.kd.c2_in) {
             // guard band: decide d <= r again from the input coordinates
             const uint32_t idx = sh_idx[k];
-            if (!pair_inside(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo, a.kd.c2r_tol,
-                             a.kd.r_rad))
+            if (!pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
+                                 a.kd.c2r_tol, a.kd.r_rad))
               w = -1.f;
           }
           if (w >= 0.f) ++npair; else w = 0.f;

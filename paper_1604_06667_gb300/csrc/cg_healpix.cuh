@@ -98,6 +98,7 @@ __device__ int ring_ranges(int64_t ns, int64_t i, const Disc* discs, int nd, Ran
   bool any = false, full = false;
   double lo = 0.0, hi = 0.0;   // hull of [pc - W, pc + W], unwrapped near the first disc
   for (int q = 0; q < nd && !full; ++q) {
+    if (discs[q].R < 0.0) continue;   // empty group
     const double hw = disc_halfwidth(discs[q].tc, discs[q].R, ta, tb);
     if (hw < 0.0) continue;
     const double W = hw + 0.5 * dphi + 1e-12;

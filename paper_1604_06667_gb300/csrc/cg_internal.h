@@ -61,6 +61,9 @@ struct Tiling {           // geometry of one tiling of the targets
   // tile centre in FP32 with the radius as a chord
   double4* sub64 = nullptr;       // [n_tiles * 4]
   float4* subf = nullptr;         // [n_tiles * 4]
+  // every tile: its 4-target groups (compact k-d leaves), FP64 centre + radius
+  // (radius < 0: an empty group); the candidate query's discs
+  double4* grp64 = nullptr;       // [n_tiles * T / 4]
   int64_t ranges_gen = -1;        // sample index the per-add ranges belong to
 };
 

@@ -18,29 +18,47 @@
 namespace cg {
 namespace {
 
-// One warp per tile; mode 0 counts ranges, mode 1 writes them.  With sub64
-// the tile's candidates are those of its four quarter discs (tighter than one
-// disc around the tile centre); otherwise one disc of radius (tile radius + r).
-__global__ void k_tile_query(const double4* __restrict__ tc64,
-                             const double4* __restrict__ sub64, int64_t n_tiles, int64_t ns,
-                             double r_rad, int64_t* __restrict__ counts,
-                             const int64_t* __restrict__ offs, Range* __restrict__ out,
-                             int mode) {
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+// One warp per tile; mode 0 counts ranges, mode 1 writes them.  The tile's
+// candidates are the samples within r of any of its 4-target groups' discs
+// (radius group radius + r): per ring, the hull of those discs' pixel
+// intervals, which follows the outline of the tile widened by r (one disc of
+// radius tile radius + r around the centre would hold ~1.4x as many samples
+// for a square tile).  Without groups: that one disc.
+constexpr int kQueryWarps = 8;
+constexpr int kMaxDiscs = 32;
+
+__global__ void __launch_bounds__(32 * kQueryWarps) k_tile_query(
+    const double4* __restrict__ tc64, const double4* __restrict__ grp64, int n_grp,
+    int64_t n_tiles, int64_t ns, double r_rad, int64_t* __restrict__ counts,
+    const int64_t* __restrict__ offs, Range* __restrict__ out, int mode) {
+  __shared__ Disc sdisc[kQueryWarps][kMaxDiscs];
+  const int64_t tile = (int64_t)blockIdx.x * kQueryWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   if (tile >= n_tiles) return;
-  Disc discs[4];
+  Disc* discs = sdisc[wq];
   int nd = 1;
-  discs[0] = make_disc(tc64[tile], r_rad);
-  if (sub64) {
-    nd = 4;
-    for (int q = 0; q < 4; ++q) discs[q] = make_disc(sub64[tile * 4 + q], r_rad);
+  if (grp64) {
+    nd = n_grp;
+    if (lane < nd) {
+      const double4 gc = grp64[tile * nd + lane];
+      Disc d = make_disc(gc, r_rad);
+      if (gc.w < 0.0) d.R = -1.0;   // empty group
+      discs[lane] = d;
+    }
+  } else if (lane == 0) {
+    discs[0] = make_disc(tc64[tile], r_rad);
   }
+  __syncwarp();
   // colatitude span of all discs
   double tlo = kPi, thi = 0.0;
   for (int q = 0; q < nd; ++q) {
+    if (discs[q].R < 0.0) continue;
     tlo = fmin(tlo, fmax(0.0, discs[q].tc - discs[q].R));
     thi = fmax(thi, fmin(kPi, discs[q].tc + discs[q].R));
+  }
+  if (thi < tlo) {  // no member at all
+    if (mode == 0 && lane == 0) counts[tile] = 0;
+    return;
   }
   int64_t ilo = (int64_t)floor(ring_coord(ns, cos(tlo))) - 2;
   int64_t ihi = (int64_t)ceil(ring_coord(ns, cos(thi))) + 2;
@@ -260,6 +278,7 @@ void tiling_free(Tiling& t, cudaStream_t s) {
   dfree(t.order, s);
   t.cap_order = 0;
   dfree(t.sub64, s);
+  dfree(t.grp64, s);
   dfree(t.subf, s);
   dfree(t.range_off, s);
   dfree(t.ranges, s);
@@ -279,9 +298,9 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   dfree(t.range_s, s);
   dfree(t.range_c, s);
   if ((e = dalloc(&counts, (size_t)nt, s)) != cudaSuccess) return e;
-  const int warps = 8;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, t.sub64, nt, g->nside, r,
-                                                        counts, nullptr, nullptr, 0);
+  const int n_grp = t.T / 4;
+  k_tile_query<<<ceil_div(nt, kQueryWarps), 32 * kQueryWarps, 0, s>>>(
+      t.c64, t.grp64, n_grp, nt, g->nside, r, counts, nullptr, nullptr, 0);
   g->n_launches += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int64_t* h = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt + 1));
@@ -301,8 +320,8 @@ cudaError_t tiles_query(cg_grid* g, Tiling& t) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   free(h);
   if (e != cudaSuccess) return e;
-  k_tile_query<<<ceil_div(nt, warps), 32 * warps, 0, s>>>(t.c64, t.sub64, nt, g->nside, r,
-                                                        nullptr, t.range_off, t.ranges, 1);
+  k_tile_query<<<ceil_div(nt, kQueryWarps), 32 * kQueryWarps, 0, s>>>(
+      t.c64, t.grp64, n_grp, nt, g->nside, r, nullptr, t.range_off, t.ranges, 1);
   g->n_launches += 1;
   dfree(counts, s);
   dfree(g->ring_off, s);

@@ -6,9 +6,9 @@
 // targets are split by a k-d tree over their unit vectors: every node is cut
 // along its widest axis at a multiple of the leaf size, so all leaves hold
 // exactly that many targets (except the last) and each leaf is a compact box.
-// The tree is cut to 128-target leaves, then each leaf into 64 + 64 and each
-// of those into 32 + 32, so a 128-tile is two 64-tiles and four 32-target
-// quarters, all compact.
+// The tree is cut to 128-target leaves, then each leaf into 64 + 64, 32 + 32
+// and on down to groups of 4, so a 128-tile is two 64-tiles, four 32-target
+// quarters and thirty-two 4-target groups, all compact (consecutive slots).
 // The tree is built level by level with one stable 64-bit radix sort per
 // level keyed by (child node, coordinate along the child's widest axis).
 // Each tile stores
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(T) k_tile_build(
     const uint32_t* __restrict__ order, float4* __restrict__ tile_chi,
     float4* __restrict__ tile_clo, double4* __restrict__ tile_c64, float4* __restrict__ tgt_a,
     uint32_t* __restrict__ tgt_perm, float4* __restrict__ tgt_e, float4* __restrict__ tgt_n,
-    double2* __restrict__ tgt_ll, double4* __restrict__ sub64, float4* __restrict__ subf) {
+    double2* __restrict__ tgt_ll, double4* __restrict__ sub64, float4* __restrict__ subf,
+    double4* __restrict__ grp64) {
   __shared__ double red[3][T];
   const int64_t tile = blockIdx.x;
   const int j = threadIdx.x;
@@ -231,6 +232,33 @@ __global__ void __launch_bounds__(T) k_tile_build(
                              (float)(2.0 * sin(0.5 * qa)));
     }
   }
+  {
+    // 4-target groups (lanes 4 g .. 4 g + 3): centroid of the valid members
+    // and their largest angular distance from it; empty groups get radius -1
+    double gx = x, gy = y, gz = z;
+    int gv = valid ? 1 : 0;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      gx += __shfl_xor_sync(0xffffffffu, gx, o);
+      gy += __shfl_xor_sync(0xffffffffu, gy, o);
+      gz += __shfl_xor_sync(0xffffffffu, gz, o);
+      gv += __shfl_xor_sync(0xffffffffu, gv, o);
+    }
+    double gn = sqrt(gx * gx + gy * gy + gz * gz);
+    if (!(gn > 1e-9)) {  // degenerate spread: the tile centre (radius still covers)
+      gx = cx; gy = cy; gz = cz; gn = 1.0;
+    }
+    gx /= gn; gy /= gn; gz /= gn;
+    double ga = 0.0;
+    if (valid) {
+      const double ex = x - gx, ey = y - gy, ez = z - gz;
+      ga = 2.0 * asin(fmin(1.0, 0.5 * sqrt(ex * ex + ey * ey + ez * ez)));
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) ga = fmax(ga, __shfl_xor_sync(0xffffffffu, ga, o));
+    ga = ga * (1.0 + 1e-9) + 1e-12;
+    if ((j & 3) == 0) grp64[tile * (T / 4) + (j >> 2)] = make_double4(gx, gy, gz, gv ? ga : -1.0);
+  }
   if (j == 0) {
     float hx, lx, hy, ly, hz, lz;
     split_f64(cx, hx, lx);
@@ -264,6 +292,7 @@ static cudaError_t tiling_alloc(Tiling& t, int T, int64_t P, cudaStream_t s) {
   if ((e = dalloc(&t.c64, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
   if ((e = dalloc(&t.a, (size_t)(t.n_tiles * T), s)) != cudaSuccess) return e;
   if ((e = dalloc(&t.tile_cand, (size_t)t.n_tiles, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&t.grp64, (size_t)(t.n_tiles * (T / 4)), s)) != cudaSuccess) return e;
   if (T == kTile2) {
     if ((e = dalloc(&t.sub64, (size_t)(t.n_tiles * 4), s)) != cudaSuccess) return e;
     if ((e = dalloc(&t.subf, (size_t)(t.n_tiles * 4), s)) != cudaSuccess) return e;
@@ -286,11 +315,11 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
   if ((e = dalloc(&g->tgt_f2, slots, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->tgt_ll, slots, s)) != cudaSuccess) return e;
 
-  // k-d tree levels: leaves of kTile2 targets, then two more levels that split
-  // every leaf into kTile halves and those into 32-target quarters
+  // k-d tree levels: leaves of kTile2 targets, then five more levels that split
+  // every leaf into kTile halves, 32-target quarters and on down to groups of 4
   int levels2 = 0;
   while (((int64_t)1 << levels2) < g->t128.n_tiles) ++levels2;
-  const int levels = levels2 + 2;
+  const int levels = levels2 + 5;
   const int64_t max_nodes = (int64_t)1 << (levels + 1);
   float4* pos = nullptr;
   uint32_t *ord = nullptr, *nid = nullptr, *child = nullptr, *val = nullptr;
@@ -313,8 +342,7 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
     g->n_launches += 1;
   }
   for (int l = 0; l < levels && e == cudaSuccess; ++l) {
-    const uint32_t leaf =
-        (l < levels2) ? (uint32_t)kTile2 : (l == levels2 ? (uint32_t)kTile : 32u);
+    const uint32_t leaf = (l < levels2) ? (uint32_t)kTile2 : ((uint32_t)kTile >> (l - levels2));
     const int64_t nchild = (int64_t)1 << (l + 1);
     e = cudaMemsetAsync(bmin, 0xff, sizeof(uint32_t) * (size_t)(3 * nchild), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bmax, 0x00, sizeof(uint32_t) * (size_t)(3 * nchild), s);
@@ -337,10 +365,10 @@ cudaError_t targets_build(cg_grid* g, const double* lon, const double* lat) {
   if (e == cudaSuccess) {
     k_tile_build<kTile2><<<(unsigned)g->t128.n_tiles, kTile2, 0, s>>>(
         lon, lat, P, ord, g->t128.chi, g->t128.clo, g->t128.c64, g->t128.a, g->tgt_perm,
-        g->tgt_e, g->tgt_n, g->tgt_ll, g->t128.sub64, g->t128.subf);
+        g->tgt_e, g->tgt_n, g->tgt_ll, g->t128.sub64, g->t128.subf, g->t128.grp64);
     k_tile_build<kTile><<<(unsigned)g->t64.n_tiles, kTile, 0, s>>>(
         lon, lat, P, ord, g->t64.chi, g->t64.clo, g->t64.c64, g->t64.a, nullptr, nullptr,
-        nullptr, nullptr, nullptr, nullptr);
+        nullptr, nullptr, nullptr, nullptr, g->t64.grp64);
     g->n_launches += 2;
     e = cudaGetLastError();
   }

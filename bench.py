@@ -288,6 +288,7 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
     return {
         "form": form, "value": upd * world / (ms_max / 1e3), "ms_per_step": ms_max,
         "pairs": pairs, "updates_per_step": upd,
+        "weights_evaluated": int(info1["n_candidates"]) * int(info1["tile_size"]),
         "hbm_roofline": {"bytes_per_step": step_bytes,
                          "achieved_gbs": step_bytes / (ms_max / 1e3) / 1e9,
                          "peak_gbs": peaks["hbm_gbs"],
@@ -567,6 +568,9 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pairs_per_step": prim["pairs"],
         "pairs_oracle": (gold or {}).get("pairs"),
+        "weights_evaluated_per_step": prim["weights_evaluated"],
+        "tile_fill": (prim["pairs"] / prim["weights_evaluated"]
+                      if prim["weights_evaluated"] else None),
         "hbm_roofline": prim["hbm_roofline"],
         "roofline": prim["roofline"],
         "stages_ms_per_step": prim["stages_ms_per_step"],

@@ -191,8 +191,10 @@ const char* cg_last_error(void);
 
 /* Counters and layout facts of a handle (host struct).
  *   nside, n_tiles, tile_size, n_ranges: planner choices;
- *   pairs_tested: (target, candidate) pairs the last add evaluated;
- *   path: the accumulation form the last add used (cg_path). */
+ *   path: the accumulation form the last add used (cg_path);
+ *   n_candidates: (tile, sample) candidate pairs of the last add, summed over
+ *                 tiles; each stands for tile_size (target, sample) weights
+ *                 (those beyond the support are zero). */
 typedef struct {
   int64_t n_targets;
   int32_t n_channels;
@@ -204,6 +206,7 @@ typedef struct {
   int64_t n_samples_total;
   int64_t n_pairs;      /* (target, sample) pairs with d <= r since the last reset */
   int64_t n_launches;   /* kernels this handle has launched since creation */
+  int64_t n_candidates;
 } cg_info;
 /* Fill *info (host struct).  Synchronises the stream (n_pairs is device-side). */
 cg_status cg_get_info(cg_grid* g, cg_info* info);

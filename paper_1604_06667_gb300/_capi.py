@@ -26,7 +26,8 @@ class CgInfo(ctypes.Structure):
                 ("nside", ctypes.c_int32), ("n_tiles", ctypes.c_int64),
                 ("tile_size", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("n_ranges", ctypes.c_int64), ("n_samples_total", ctypes.c_int64),
-                ("n_pairs", ctypes.c_int64), ("n_launches", ctypes.c_int64)]
+                ("n_pairs", ctypes.c_int64), ("n_launches", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64)]
 
 CG_N_STAGES = 5
 STAGE_NAMES = ("keys", "sort", "index", "grid", "finalize")

@@ -3,6 +3,7 @@
 // the handle's stream.
 #include <cmath>
 #include <cstdarg>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -621,6 +622,17 @@ cg_status cg_get_info(cg_grid* g, cg_info* info) {
           "cg_get_info");
   CG_CUDA(cudaStreamSynchronize(g->stream), "cg_get_info");
   info->n_pairs = (int64_t)pairs;
+  info->n_candidates = 0;
+  const Tiling& t = tc ? g->t128 : g->t64;
+  if (t.tile_cand && t.ranges_gen == g->index_gen && t.n_tiles > 0) {
+    std::vector<int32_t> h((size_t)t.n_tiles);
+    CG_CUDA(cudaMemcpy(h.data(), t.tile_cand, sizeof(int32_t) * (size_t)t.n_tiles,
+                       cudaMemcpyDeviceToHost),
+            "cg_get_info");
+    int64_t sum = 0;
+    for (int32_t v : h) sum += v;
+    info->n_candidates = sum;
+  }
   return CG_OK;
 }
 

@@ -97,7 +97,12 @@ int64_t or_ang2pix_ring(int64_t ns, double lon_deg, double lat_deg) {
     const double v = dns * (z * 0.75);
     const int64_t asc = (int64_t)(u - v);       /* ascending line index  */
     const int64_t dsc = (int64_t)(u + v);       /* descending line index */
-    const int64_t k = ns + 1 + asc - dsc;       /* belt ring from z=2/3, 1..2ns+1 */
+    int64_t k = ns + 1 + asc - dsc;             /* belt ring from z=2/3, 1..2ns+1 */
+    /* a point on the boundary ring |z| = 2/3 whose longitude is a pixel
+     * corner can round to ring 0 or 2ns+2, outside the belt: it belongs to
+     * the boundary ring (Gorski et al. 2005: belt rings are 1 .. 2ns+1) */
+    if (k < 1) k = 1;
+    if (k > 2 * ns + 1) k = 2 * ns + 1;
     const int64_t odd = k & 1;
     int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
     j = j % (4 * ns);
@@ -108,7 +113,8 @@ int64_t or_ang2pix_ring(int64_t ns, double lon_deg, double lat_deg) {
     const double x = dns * sqrt(3.0 * (1.0 - za));
     const int64_t a = (int64_t)(t * x);
     const int64_t b = (int64_t)((1.0 - t) * x);
-    const int64_t k = a + b + 1;                /* ring counted from the pole */
+    int64_t k = a + b + 1;                      /* ring counted from the pole */
+    if (k > ns) k = ns;                         /* the same boundary: cap rings 1 .. ns */
     int64_t j = (int64_t)(tt * (double)k);
     j = j % (4 * k);
     if (j < 0) j += 4 * k;

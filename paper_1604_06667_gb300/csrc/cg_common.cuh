@@ -57,7 +57,11 @@ __device__ __forceinline__ int64_t ang2pix_ring_f64(int64_t ns, double lon_deg, 
     const double v = __dmul_rn(dns, __dmul_rn(z, 0.75));
     const int64_t asc = (int64_t)__dsub_rn(u, v);
     const int64_t dsc = (int64_t)__dadd_rn(u, v);
-    const int64_t k = ns + 1 + asc - dsc;
+    int64_t k = ns + 1 + asc - dsc;
+    // a point on the boundary ring |z| = 2/3 at a pixel-corner longitude can
+    // round to ring 0 or 2 ns + 2, outside the belt: it belongs to the
+    // boundary ring (belt rings are 1 .. 2 ns + 1)
+    k = k < 1 ? 1 : (k > 2 * ns + 1 ? 2 * ns + 1 : k);
     const int64_t odd = k & 1;
     int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
     j %= 4 * ns;
@@ -69,7 +73,8 @@ __device__ __forceinline__ int64_t ang2pix_ring_f64(int64_t ns, double lon_deg, 
     const double x = __dmul_rn(dns, __dsqrt_rn(__dmul_rn(3.0, __dsub_rn(1.0, za))));
     const int64_t a = (int64_t)__dmul_rn(t, x);
     const int64_t b = (int64_t)__dmul_rn(__dsub_rn(1.0, t), x);
-    const int64_t k = a + b + 1;
+    int64_t k = a + b + 1;
+    if (k > ns) k = ns;   // the same boundary: cap rings are 1 .. ns
     int64_t j = (int64_t)__dmul_rn(tt, (double)k);
     j %= 4 * k;
     if (j < 0) j += 4 * k;

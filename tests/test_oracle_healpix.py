@@ -126,6 +126,54 @@ def test_pixel_box_contains_point(ns):
         assert abs(dphi) <= math.pi / c + 1e-12
 
 
+@pytest.mark.parametrize("ns", [1, 4, 64, 256])
+def test_boundary_ring_corners(ns):
+    """Points on the cap/belt boundary |z| = 2/3 at pixel-corner longitudes
+    (and one ulp either side) get a pixel whose box holds them (a corner
+    belongs to the pixels that meet there, on the boundary ring or the next
+    belt ring): the belt formula alone can round such a point to ring 0 or
+    2 ns + 2, outside the belt, i.e. a pixel of the neighbouring cap ring
+    several spacings away."""
+    zb = 2.0 / 3.0
+    for sign in (1.0, -1.0):
+        lat0 = math.degrees(math.asin(sign * zb))
+        lats = np.array([lat0, np.nextafter(lat0, 90.0), np.nextafter(lat0, -90.0)])
+        lon0 = np.arange(0, 4 * ns + 1) * (90.0 / ns)
+        lons = np.concatenate([lon0, np.nextafter(lon0, 400.0), np.nextafter(lon0, -400.0)])
+        lon, lat = np.meshgrid(lons, lats)
+        lon, lat = lon.ravel(), lat.ravel()
+        pix = oracle.ang2pix(ns, lon, lat)
+        zz = np.sin(np.radians(lat))
+        for k in range(pix.size):
+            r = oracle.pix2ring(ns, int(pix[k]))
+            c, f, zc, ph = oracle.ring_info(ns, r)
+            zn = 1.0 if r == 1 else oracle.ring_info(ns, r - 1)[2]
+            zs = -1.0 if r == 4 * ns - 1 else oracle.ring_info(ns, r + 1)[2]
+            assert zs - 1e-12 <= zz[k] <= zn + 1e-12
+            phic = (pix[k] - f + ph) * 2 * math.pi / c
+            dphi = (math.radians(lon[k]) - phic + math.pi) % (2 * math.pi) - math.pi
+            assert abs(dphi) <= math.pi / c + 1e-12
+
+
+def test_lookup_equals_bruteforce_on_sightlines():
+    """The lookup oracle finds every pair the brute force finds when the
+    targets are the pixel centres of a coarser HEALPix grid -- they sit on
+    ring latitudes and pixel corners of the lookup's finer grid (the cap /
+    belt boundary ring included)."""
+    import workloads
+    lon_t, lat_t = workloads.healpix_centres(8)
+    rng = np.random.Generator(np.random.PCG64(29))
+    n = 30000
+    lat = np.degrees(np.arcsin(rng.uniform(-1, 1, n)))
+    lon = rng.uniform(0, 360, n)
+    data = rng.normal(size=(n, 1))
+    k = oracle.gauss1d(2.0, 6.0)
+    a = oracle.grid_lookup(64, lon_t, lat_t, lon, lat, data, k)
+    b = oracle.grid_bruteforce(lon_t, lat_t, lon, lat, data, k)
+    assert a.npairs == b.npairs
+    assert np.allclose(a.wsum, b.wsum, rtol=1e-12, atol=0)
+
+
 def test_lon_fold_and_poles():
     ns = 16
     lat = np.array([10.0, 10.0, 10.0, 10.0, 90.0, -90.0, 0.0])

@@ -512,6 +512,88 @@ def time_example1(args, dev):
             "paper_16_cores_s": 67.0, "speedup_vs_paper_16_cores": 67.0e3 / ms}
 
 
+def time_sightline(args, dev):
+    """Appendix A.1 of the paper: ~4.7e7 samples uniform on the sphere (1024
+    PSF-convolved point sources + noise) gridded onto the 3,145,728 pixel
+    centres of an nside-512 HEALPix grid (sight-line targets), kernel FWHM
+    13.7'.  One-shot calls timed with CUDA events."""
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder
+    lon, lat, data, lon_t, lat_t, kern, support, maxres, meta = workloads.sightline_device(dev)
+    g = Gridder(lon_t, lat_t, n_channels=1, device=dev)
+    g.set_kernel("gauss1d", (kern["sigma"],), support, maxres)
+    out = torch.empty((g.n_targets, 1), device=dev)
+    w = torch.empty(g.n_targets, device=dev)
+    for _ in range(2):
+        g.grid_oneshot(lon, lat, data, out=out, out_weights=w)
+    g.sync()
+    g.set_timing(True)
+    g.read_timing()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 3
+    e0.record(stream)
+    for _ in range(steps):
+        g.grid_oneshot(lon, lat, data, out=out, out_weights=w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stages = g.read_timing()
+    info = g.info()
+    g.close()
+    return {"workload": "paper App. A.1: %d samples uniform on the sphere -> %d HEALPix nside-%d "
+                        "pixel centres, kernel FWHM %.2f', support 3 sigma, one channel"
+                        % (lon.numel(), lon_t.size, meta["nside_targets"],
+                           meta["fwhm_kernel_deg"] * 60.0),
+            "ms_per_call": ms, "pairs_per_call": info["n_pairs"],
+            "updates_per_s": info["n_pairs"] / (ms / 1e3),
+            "stages_ms": {k: v / steps for k, v in stages.items() if k != "grid_launches"}}
+
+
+def study_aliasing(args, dev):
+    """Appendix A.2 of the paper: scan lines 0.2-0.5 PSF apart gridded with
+    kernels of 0.3-0.7 PSF (FWHM), support 5 and 3 sigma, over a 1.5 x 1.5
+    deg field with PSF / 20 pixels; max |R - T| / T against the field
+    convolved with the kernel (T).  The paper prints these only as figures."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1604_06667_gb300 import Gridder
+    table, t_gpu = {}, 0.0
+    truths = {}
+    for fs in (0.2, 0.3, 0.4, 0.5):
+        row = {}
+        for fk in (0.3, 0.4, 0.5, 0.6, 0.7):
+            cell = {}
+            for ssig in (5.0, 3.0):
+                wl = workloads.aliasing(fs, fk, support_sigmas=ssig)
+                if fk not in truths:
+                    truths[fk] = workloads.aliasing_truth(wl)
+                g = Gridder(wl.lon_t, wl.lat_t, n_channels=1, device=dev)
+                g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
+                d = torch.from_numpy(wl.data).to(dev)
+                lon = torch.from_numpy(wl.lon_s).to(dev)
+                lat = torch.from_numpy(wl.lat_s).to(dev)
+                out = torch.empty((wl.n_targets, 1), device=dev)
+                g.grid_oneshot(lon, lat, d, out=out)
+                g.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.grid_oneshot(lon, lat, d, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                t_gpu += e0.elapsed_time(e1)
+                r = out[:, 0].cpu().numpy().astype(np.float64)
+                g.close()
+                cell["support_%dsigma" % int(ssig)] = float(np.max(np.abs(r - truths[fk]) / truths[fk]))
+            row["kernel_%.1f" % fk] = cell
+        table["spacing_%.1f" % fs] = row
+    return {"workload": "paper App. A.2: scan lines, 1.5 x 1.5 deg, PSF 0.1 deg, pixel PSF/20, "
+                        "no noise; max relative deviation from the kernel-convolved field",
+            "max_rel_deviation": table, "gpu_ms_total": t_gpu}
+
+
 def grid_kernel_bytes(wl, dbytes):
     """Algorithmic bytes of one gridder launch: every sample's channel row and
     its sorted 32-byte position record read once, the map and weight map
@@ -589,6 +671,10 @@ def main():
         line["batched"] = time_batched(args, dev)
         progress("paper example 1")
         line["paper_example1"] = time_example1(args, dev)
+        progress("paper appendix A.1 (HEALPix sight lines)")
+        line["paper_sightline_a1"] = time_sightline(args, dev)
+        progress("paper appendix A.2 (scan-line aliasing study)")
+        line["paper_aliasing_a2"] = study_aliasing(args, dev)
         progress("plain 2-D and all-sky")
         line["plain2d"] = time_config(args, dev, "plain2d")
         line["allsky"] = time_config(args, dev, "allsky")

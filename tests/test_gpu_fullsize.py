@@ -9,7 +9,10 @@ sampled target, found by a latitude-band prefilter that is a superset):
 * all-sky elliptical (1e7 x 32 -> 4096 x 2048);
 * the differentiable workload (2e5 x 16 -> 256^2): forward map, adjoint
   (degridding) on sampled samples, d/dsigma on sampled targets, and a
-  non-increasing 50-step map-making loss.
+  non-increasing 50-step map-making loss;
+* the paper's Example 1 (1e8 samples) and its Appendix A.1 sight-line
+  simulation (4.7e7 samples onto the 3,145,728 pixel centres of an nside-512
+  HEALPix grid).
 """
 import json
 import os
@@ -175,5 +178,27 @@ def test_paper_example1_full_sampled():
     wl = _host_wl(lon, lat, data, lon_t, lat_t, kern, support)
     del lon, lat, data
     tsel = np.unique(np.concatenate([_sampled_targets(wl, 24, 607), [0, lon_t.size - 1]]))
+    ref, _ = oracle_on_targets(wl, tsel, oracle.gauss1d(kern["sigma"], support))
+    compare_maps(out_np[tsel], w_np[tsel], ref, tol=FP32_TOL)
+
+
+def test_paper_sightline_a1_full_sampled():
+    """Appendix A.1 at full size: samples uniform on the sphere onto HEALPix
+    sight lines (arbitrary targets, tiles from the k-d tree), sampled targets
+    including the first and last pixel (the poles' rings)."""
+    import torch
+    from paper_1604_06667_gb300 import Gridder
+    lon, lat, data, lon_t, lat_t, kern, support, maxres, meta = workloads.sightline_device("cuda")
+    assert meta["nside_targets"] == 512 and lon_t.size == 12 * 512 * 512
+    g = Gridder(lon_t, lat_t, n_channels=1)
+    g.set_kernel("gauss1d", (kern["sigma"],), support, maxres)
+    w = torch.empty(lon_t.size, device="cuda")
+    out = g.grid_oneshot(lon, lat, data, out_weights=w)
+    g.sync()
+    out_np, w_np = out.cpu().numpy(), w.cpu().numpy()
+    g.close()
+    wl = _host_wl(lon, lat, data, lon_t, lat_t, kern, support)
+    del lon, lat, data
+    tsel = np.unique(np.concatenate([_sampled_targets(wl, 24, 611), [0, lon_t.size - 1]]))
     ref, _ = oracle_on_targets(wl, tsel, oracle.gauss1d(kern["sigma"], support))
     compare_maps(out_np[tsel], w_np[tsel], ref, tol=FP32_TOL)

@@ -352,3 +352,173 @@ def example1_device(device, n: int = 100_000_000, seed: int | None = None):
     sigma = 300.0 * ARCSEC / math.sqrt(8.0 * math.log(2.0))
     return lon, lat, data, lon_t, lat_t, {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, \
         sigma / 2.0
+
+
+# ---------------------------------------------------------------------------
+# Appendix A.1: point sources on the sphere gridded onto HEALPix sight lines
+# ---------------------------------------------------------------------------
+def healpix_centres(nside: int):
+    """Longitude / latitude (degrees) of the RING-scheme pixel centres of a
+    HEALPix tessellation (Gorski et al. 2005): rings of constant z, 4 i
+    pixels on polar-cap ring i, 4 nside on the equatorial rings, whose
+    longitudes start at 0 or half a pixel on alternate rings.  Target
+    positions only (input synthesis)."""
+    ns = int(nside)
+    lon_parts, lat_parts = [], []
+    for i in range(1, 4 * ns):
+        if i < ns:                      # north cap
+            z = 1.0 - i * i / (3.0 * ns * ns)
+            m = 4 * i
+            phi = (np.arange(m) + 0.5) * (2.0 * math.pi / m)
+        elif i <= 3 * ns:               # equatorial belt
+            z = 4.0 / 3.0 - 2.0 * i / (3.0 * ns)
+            m = 4 * ns
+            s = (i - ns + 1) % 2
+            phi = (np.arange(m) + 0.5 * s) * (2.0 * math.pi / m)
+        else:                           # south cap
+            k = 4 * ns - i
+            z = -(1.0 - k * k / (3.0 * ns * ns))
+            m = 4 * k
+            phi = (np.arange(m) + 0.5) * (2.0 * math.pi / m)
+        lon_parts.append(np.degrees(phi))
+        lat_parts.append(np.full(m, math.degrees(math.asin(z))))
+    return np.concatenate(lon_parts), np.concatenate(lat_parts)
+
+
+def _unit(lon_deg, lat_deg, xp=np):
+    l = lon_deg * (math.pi / 180.0)
+    b = lat_deg * (math.pi / 180.0)
+    return xp.stack([xp.cos(b) * xp.cos(l), xp.cos(b) * xp.sin(l), xp.sin(b)], -1)
+
+
+def sightline_device(device, scale: float = 1.0, seed: int | None = None, n_sources: int = 1024):
+    """The simulation of Appendix A.1: 1024 point sources at random positions
+    on the sphere (amplitudes U[1, 10]) seen through a Gaussian PSF of FWHM
+    4 pixel sizes, sampled at 15 x npix random positions uniform on the
+    sphere with N(0, 1) noise added to every sample, and gridded onto the
+    pixel centres of a HEALPix grid with a Gaussian kernel of half the PSF's
+    FWHM (support 3 sigma, hpx_maxres sigma / 2).  nside = 512 at scale 1
+    (npix 3,145,728, ~4.7e7 samples, PSF 27.5', kernel 13.7'), nside 512
+    sqrt(scale) rounded to a power of two otherwise.  Samples, sources and
+    signal are drawn and evaluated on the device (torch, seeded).
+    Returns (lon, lat, data[n, 1] float32, lon_t, lat_t, kernel dict,
+    support, hpx_maxres, meta)."""
+    import torch
+    ns = 512
+    while ns > 8 and (ns // 2) ** 2 >= 512 * 512 * scale:
+        ns //= 2
+    npix = 12 * ns * ns
+    n = 15 * npix
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE + 7 if seed is None else seed)
+    z = torch.rand(n, generator=gen, device=device, dtype=torch.float64) * 2.0 - 1.0
+    lon = torch.rand(n, generator=gen, device=device, dtype=torch.float64) * 360.0
+    lat = torch.rad2deg(torch.asin(z))
+    zs = torch.rand(n_sources, generator=gen, device=device, dtype=torch.float64) * 2.0 - 1.0
+    ls = torch.rand(n_sources, generator=gen, device=device, dtype=torch.float64) * 360.0
+    amp = 1.0 + 9.0 * torch.rand(n_sources, generator=gen, device=device, dtype=torch.float64)
+    pix = math.sqrt(4.0 * math.pi / npix)                 # pixel size (rad)
+    fwhm_psf = 4.0 * pix
+    s2 = 8.0 * math.log(2.0)
+    sig_psf = fwhm_psf / math.sqrt(s2)
+    vs = _unit(ls, torch.rad2deg(torch.asin(zs)), torch).to(torch.float32)     # [S, 3]
+    data = torch.randn((n, 1), generator=gen, device=device, dtype=torch.float32)
+    chunk = 1 << 17
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        u = _unit(lon[a:b], lat[a:b], torch).to(torch.float32)                  # [c, 3]
+        c2 = (2.0 - 2.0 * (u @ vs.T)).clamp_min(0.0)                           # chord^2
+        data[a:b, 0] += (torch.exp(-c2 / (2.0 * sig_psf * sig_psf)) * amp.to(torch.float32)).sum(1)
+    lon_t, lat_t = healpix_centres(ns)
+    sigma = math.degrees(0.5 * fwhm_psf / math.sqrt(s2))
+    meta = {"nside_targets": ns, "npix": npix, "n_samples": n, "fwhm_psf_deg": math.degrees(fwhm_psf),
+            "fwhm_kernel_deg": math.degrees(0.5 * fwhm_psf)}
+    return lon, lat, data, lon_t, lat_t, {"type": "gauss1d", "sigma": sigma}, 3.0 * sigma, \
+        sigma / 2.0, meta
+
+
+# ---------------------------------------------------------------------------
+# Appendix A.2: scan lines of samples, kernel size against aliasing
+# ---------------------------------------------------------------------------
+def aliasing(f_space: float, f_kernel: float, support_sigmas: float = 5.0,
+             seed: int | None = None, side: float = 1.5, psf: float = 0.1,
+             pix_div: int = 20, along_div: int = 100, n_sources: int = 2000) -> Workload:
+    """The stripe simulation of Appendix A.2: a quasi-continuous field of
+    point sources (uniform positions over the field and a margin, amplitudes
+    U[0.5, 1.5]) seen through a Gaussian PSF of FWHM ``psf`` deg, sampled on
+    horizontal scan lines ``f_space * psf`` apart with ``psf / along_div``
+    spacing along them (no noise), gridded onto ``psf / pix_div`` pixels over
+    ``side`` x ``side`` deg with a Gaussian kernel of FWHM ``f_kernel * psf``
+    and support ``support_sigmas`` sigma.  The samples cover the field plus
+    the largest support of the study (5 sigma of a 0.7 psf kernel) and do not
+    depend on the kernel.  ``meta`` holds the sources, for aliasing_truth()."""
+    lon, lat, val, src, sig_psf = _aliasing_samples(float(f_space), seed, side, psf, along_div,
+                                                    n_sources)
+    s2 = math.sqrt(8.0 * math.log(2.0))
+    sig_k = f_kernel * psf / s2
+    npx = int(round(side * pix_div / psf))
+    lon_t, lat_t = car_grid(120.0, 30.0, npx, npx, side / npx)
+    return Workload("aliasing", lon, lat, val[:, None], None, lon_t, lat_t,
+                    {"type": "gauss1d", "sigma": sig_k}, support_sigmas * sig_k, sig_k / 2.0,
+                    (npx, npx),
+                    {"f_space": f_space, "f_kernel": f_kernel, "support_sigmas": support_sigmas,
+                     "sig_psf": sig_psf, "src": src})
+
+
+_ALIAS_CACHE: dict = {}
+
+
+def _aliasing_samples(f_space, seed, side, psf, along_div, n_sources):
+    key = (f_space, seed, side, psf, along_div, n_sources)
+    if key in _ALIAS_CACHE:
+        return _ALIAS_CACHE[key]
+    rng = rng_for(8, seed)
+    lon0, lat0 = 120.0, 30.0
+    s2 = math.sqrt(8.0 * math.log(2.0))
+    sig_psf = psf / s2
+    reach = 5.0 * 0.7 * psf / s2           # largest support of the study
+    margin = 6.0 * sig_psf + reach
+    span = side + 2.0 * margin
+    dl = span / math.cos(math.radians(lat0))
+    src_lon = lon0 + (rng.random(n_sources) - 0.5) * dl
+    src_lat = lat0 + (rng.random(n_sources) - 0.5) * span
+    src_amp = rng.uniform(0.5, 1.5, n_sources)
+    ext = side + 2.0 * reach
+    n_lines = int(math.floor(ext / (f_space * psf))) + 1
+    lats = lat0 - 0.5 * ext + np.arange(n_lines) * (f_space * psf)
+    ext_lon = ext / math.cos(math.radians(lat0))
+    n_along = int(round(ext * along_div / psf)) + 1
+    lons = lon0 - 0.5 * ext_lon + np.arange(n_along) * (ext_lon / (n_along - 1))
+    lat, lon = np.meshgrid(lats, lons, indexing="ij")
+    lon = lon.ravel().astype(np.float64)
+    lat = lat.ravel().astype(np.float64)
+    val = _gauss_field(_unit(lon, lat), src_lon, src_lat, src_amp, sig_psf, 1.0).astype(np.float32)
+    out = (lon, lat, val, (src_lon, src_lat, src_amp), sig_psf)
+    _ALIAS_CACHE.clear()
+    _ALIAS_CACHE[key] = out
+    return out
+
+
+def aliasing_truth(wl: Workload) -> np.ndarray:
+    """The field of an aliasing() workload convolved with its (unit-integral)
+    gridding kernel, at the targets: each PSF-convolved source becomes a
+    Gaussian of variance sigma_psf^2 + sigma_k^2 and peak scaled by
+    sigma_psf^2 / (sigma_psf^2 + sigma_k^2) (small-field approximation; the
+    kernel's truncation at its support is ignored)."""
+    src_lon, src_lat, src_amp = wl.meta["src"]
+    sp, sk = wl.meta["sig_psf"], wl.kernel["sigma"]
+    st2 = sp * sp + sk * sk
+    return _gauss_field(_unit(wl.lon_t, wl.lat_t), src_lon, src_lat, src_amp, math.sqrt(st2),
+                        sp * sp / st2)
+
+
+def _gauss_field(u, src_lon, src_lat, src_amp, sig, scale):
+    """sum_k scale * amp_k * exp(-d^2 / 2 sig^2) at the unit vectors u
+    (sources beyond 8 sig ignored; sig in degrees)."""
+    from scipy.spatial import cKDTree
+    vs = _unit(src_lon, src_lat)
+    reach = 2.0 * math.sin(math.radians(8.0 * sig) / 2.0)
+    m = cKDTree(u).sparse_distance_matrix(cKDTree(vs), reach, output_type="coo_matrix")
+    d2 = np.degrees(2.0 * np.arcsin(np.minimum(1.0, 0.5 * m.data))) ** 2
+    w = scale * src_amp[m.col] * np.exp(-d2 / (2.0 * sig * sig))
+    return np.bincount(m.row, weights=w, minlength=u.shape[0])

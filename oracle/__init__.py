@@ -15,6 +15,8 @@ plain-numpy helpers that follow the paper's definitions:
 * Adjoint and d/dsigma of the normalised operator: ``degrid_bruteforce``,
   ``dsigma_bruteforce``; the dense operator ``operator_matrix`` and the
   gradient-descent map-making loop ``mapmaking_gd`` built on them.
+* Variants: normalised interpolation map -> samples (``interp_bruteforce``)
+  and one weight per sample and channel (``grid_bruteforce_pcw``).
 """
 from __future__ import annotations
 
@@ -94,6 +96,9 @@ def lib():
         L.or_degrid_bruteforce.restype = ctypes.c_int
         L.or_degrid_bruteforce.argtypes = [_i64, _pd, _pd, _i64, _pd, _pd, _i32, _pd,
                                            ctypes.POINTER(Kernel), _pd, _pd]
+        L.or_interp_bruteforce.restype = ctypes.c_int
+        L.or_interp_bruteforce.argtypes = [_i64, _pd, _pd, _i64, _pd, _pd, _i32,
+                                           ctypes.POINTER(Kernel), _pd, _pd, _pd]
         L.or_dsigma_bruteforce.restype = ctypes.c_int
         L.or_dsigma_bruteforce.argtypes = [_i64, _pd, _pd, _i64, _pd, _pd, _i32, _pd, _pd,
                                            ctypes.POINTER(Kernel), _pd]
@@ -294,6 +299,43 @@ def degrid_bruteforce(lon_t, lat_t, lon_s, lat_s, y, k: Kernel, omega=None) -> n
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return out
+
+
+def interp_bruteforce(lon_t, lat_t, lon_s, lat_s, y, k: Kernel):
+    """Normalised interpolation of the map y [P, C] at the samples:
+    xhat[n] = sum_p w_pn y_p / V_n, V_n = sum_p w_pn (d_pn <= r); NaN where
+    V_n = 0.  Returns (xhat [N, C], V [N])."""
+    lt, plt = _d(lon_t)
+    bt, pbt = _d(lat_t)
+    ls, pls = _d(lon_s)
+    bs, pbs = _d(lat_s)
+    y = np.asarray(y, dtype=np.float64)
+    if y.ndim == 1:
+        y = y[:, None]
+    C = y.shape[1]
+    yy, py = _d(y)
+    out = np.empty((ls.size, C))
+    v = np.empty(ls.size)
+    rc = lib().or_interp_bruteforce(lt.size, plt, pbt, ls.size, pls, pbs, C, ctypes.byref(k), py,
+                                    out.ctypes.data_as(_pd), v.ctypes.data_as(_pd))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out, v
+
+
+def grid_bruteforce_pcw(lon_t, lat_t, lon_s, lat_s, data, k: Kernel, omega_pc):
+    """Eq. 1-3 with one weight per sample and channel (omega_pc [N, C]):
+    N_pc = sum_n omega_nc w_pn D_nc, W_pc = sum_n omega_nc w_pn, R = N / W
+    (NaN where W_pc = 0), channel by channel through grid_bruteforce.
+    Returns (R [P, C], W [P, C], S [P, C])."""
+    data = np.asarray(data, dtype=np.float64)
+    om = np.asarray(omega_pc, dtype=np.float64)
+    P, C = np.asarray(lon_t).size, data.shape[1]
+    R, W, S = np.empty((P, C)), np.empty((P, C)), np.empty((P, C))
+    for c in range(C):
+        res = grid_bruteforce(lon_t, lat_t, lon_s, lat_s, data[:, c:c + 1], k, om[:, c])
+        R[:, c], W[:, c], S[:, c] = res.out[:, 0], res.wsum, res.sabs[:, 0]
+    return R, W, S
 
 
 def dsigma_bruteforce(lon_t, lat_t, lon_s, lat_s, data, k: Kernel, omega=None) -> np.ndarray:

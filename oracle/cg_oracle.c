@@ -635,6 +635,35 @@ int or_degrid_bruteforce(int64_t P, const double* lon_t, const double* lat_t, in
   return 0;
 }
 
+/* Normalised interpolation (map -> samples; the degridding reading in which
+ * each sample gets the kernel-weighted mean of the map around it, the mirror
+ * of Eq. 1-3): xhat[n][c] = sum_p w_pn y[p][c] / V_n, V_n = sum_p w_pn over
+ * the targets with d_pn <= r; NaN where V_n = 0.  Sample weights do not
+ * enter.  vsum[n] = V_n (may be NULL). */
+int or_interp_bruteforce(int64_t P, const double* lon_t, const double* lat_t, int64_t N,
+                         const double* lon_s, const double* lat_s, int32_t C,
+                         const or_kernel* k, const double* y, double* xhat, double* vsum) {
+  or_acc* ax = (or_acc*)calloc((size_t)(C > 0 ? C : 1), sizeof(or_acc));
+  if (!ax) return 1;
+  for (int64_t n = 0; n < N; ++n) {
+    or_acc av = {0.0, 0.0};
+    for (int32_t c = 0; c < C; ++c) ax[c] = av;
+    for (int64_t p = 0; p < P; ++p) {
+      int inside;
+      double d;
+      const double w = kernel_eval(k, lon_t[p], lat_t[p], lon_s[n], lat_s[n], &inside, &d);
+      if (!inside) continue;
+      acc_add(&av, w);
+      for (int32_t c = 0; c < C; ++c) acc_add(&ax[c], w * y[p * C + c]);
+    }
+    const double V = acc_get(&av);
+    for (int32_t c = 0; c < C; ++c) xhat[n * C + c] = (V > 0.0) ? acc_get(&ax[c]) / V : NAN;
+    if (vsum) vsum[n] = V;
+  }
+  free(ax);
+  return 0;
+}
+
 /* d R_pc / d sigma for the circular Gaussian with the support r held fixed:
  * w' = dw/dsigma = w d^2 / sigma^3 (d and sigma in degrees), and
  * dR/dsigma = (sum_n omega w' D - R sum_n omega w') / W. */

@@ -267,6 +267,39 @@ cg_status cg_set_f32_shape(cg_grid* g, int32_t shape);
 cg_status cg_degrid(cg_grid* g, const float* map, const float* map_weights, float* out,
                     int64_t n);
 
+/* Normalised interpolation of a map at the samples of the last add (the
+ * degridding reading in which every sample receives the kernel-weighted mean
+ * of the map around it; the mirror of Eq. 1-3 with targets and samples
+ * exchanged):
+ *   out[n][c] = sum_p w_pn map[p][c] / V_n,  V_n = sum_p w_pn  (d_pn <= r),
+ * NaN where no target lies within r of the sample.  The samples' weights do
+ * not enter.
+ *   map          device float32 [n_targets][C] (user order).
+ *   out          device float32 [n][C] in the add's sample order.
+ *   out_weights  device float32 [n] (V_n), or NULL.
+ *   n            must equal the last add's n_samples.
+ * Deterministic.  Asynchronous; CG_ESTATE without a previous add. */
+cg_status cg_interp(cg_grid* g, const float* map, float* out, float* out_weights, int64_t n);
+
+/* One-shot gridding with one weight per sample AND channel (an extension of
+ * Eq. 1-3: omega_n becomes omega_nc):
+ *   N_pc = sum_n omega_nc w_pn D_nc,  W_pc = sum_n omega_nc w_pn,
+ *   R_pc = N_pc / W_pc (NaN where W_pc = 0).
+ *   pc_weights   device float32 [n_samples][C], finite and >= 0; a zero
+ *                weight removes the sample from that channel (its value is
+ *                not read, so it may be NaN).
+ *   out          device float32 [n_targets][C] (layout 0) or [C][n_targets].
+ *   out_weights  device float32 [n_targets][C] or [C][n_targets] (W_pc, same
+ *                layout), or NULL.
+ * Runs the FP32 CUDA-core gridder once over 2C values per sample
+ * (omega_nc D_nc and omega_nc); builds a new sample index (cg_degrid and
+ * cg_interp then refer to these samples) and leaves the accumulators of
+ * cg_grid_add untouched.  Asynchronous. */
+cg_status cg_grid_oneshot_pcw(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                              const void* data, int32_t data_dtype, const float* pc_weights,
+                              int64_t n_samples, float* out, int32_t layout_channel_major,
+                              float* out_weights);
+
 /* Derivative of the normalised map with respect to the kernel width, for the
  * circular gauss1d kernel with the support radius held fixed:
  *   dR_pc/dsigma = (sum_n omega_n w'_pn D_nc - R_pc sum_n omega_n w'_pn) / W_p,

@@ -61,6 +61,8 @@ SIGNATURES = {
     "cg_grid_finalize": [_vp, _vp, _i32, _vp],
     "cg_grid_oneshot": [_vp, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _i32, _vp],
     "cg_grid_oneshot_host": [_vp, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _i32, _vp],
+    "cg_grid_oneshot_pcw": [_vp, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _i32, _vp],
+    "cg_interp": [_vp, _vp, _vp, _vp, _i64],
     "cg_grid_reset": [_vp],
     "cg_grid_destroy": [_vp],
     "cg_set_stream": [_vp, _vp],
@@ -130,6 +132,8 @@ cg_grid_add = _call("cg_grid_add")
 cg_grid_finalize = _call("cg_grid_finalize")
 cg_grid_oneshot = _call("cg_grid_oneshot")
 cg_grid_oneshot_host = _call("cg_grid_oneshot_host")
+cg_grid_oneshot_pcw = _call("cg_grid_oneshot_pcw")
+cg_interp = _call("cg_interp")
 cg_grid_reset = _call("cg_grid_reset")
 cg_grid_destroy = _call("cg_grid_destroy")
 cg_set_stream = _call("cg_set_stream")

@@ -135,6 +135,10 @@ void free_all(cg_grid* g) {
   dfree(g->ds_num0, s);
   dfree(g->ds_w0, s);
   dfree(g->ds_part, s);
+  dfree(g->pcw_data, s);
+  dfree(g->pcw_acc, s);
+  dfree(g->pcw_w, s);
+  g->pcw_cap_data = 0;
   dfree(g->part_num, s);
   dfree(g->part_w, s);
   dfree(g->acc_num, s);
@@ -700,6 +704,67 @@ cg_status cg_degrid(cg_grid* g, const float* map, const float* map_weights, floa
                 where);
   CG_CUDA(cudaSetDevice(g->device), where);
   CG_CUDA(grid_degrid(g, map, map_weights, out), where);
+  return CG_OK;
+}
+
+cg_status cg_interp(cg_grid* g, const float* map, float* out, float* out_weights, int64_t n) {
+  g_last_error.clear();
+  const char* where = "cg_interp";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (!g->index_valid)
+    return fail(CG_ESTATE, "%s: no sample index: call cg_grid_add (or oneshot) first", where);
+  if (n != g->last_n)
+    return fail(CG_EINVAL, "%s: n (%lld) must equal the last add's n_samples (%lld)", where,
+                (long long)n, (long long)g->last_n);
+  if (!map || !out) return fail(CG_EINVAL, "%s: null map or out pointer", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  CG_CUDA(grid_degrid(g, map, nullptr, out, true, out_weights), where);
+  return CG_OK;
+}
+
+cg_status cg_grid_oneshot_pcw(cg_grid* g, const double* lon_deg, const double* lat_deg,
+                              const void* data, int32_t data_dtype, const float* pc_weights,
+                              int64_t n_samples, float* out, int32_t layout_channel_major,
+                              float* out_weights) {
+  g_last_error.clear();
+  const char* where = "cg_grid_oneshot_pcw";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (!g->kernel_set) return fail(CG_ESTATE, "%s: call cg_set_kernel first", where);
+  if (data_dtype != CG_F32 && data_dtype != CG_BF16)
+    return fail(CG_EINVAL, "%s: data_dtype must be CG_F32 or CG_BF16", where);
+  if (n_samples < 0 || n_samples > 0x7fffffffLL)
+    return fail(CG_EINVAL, "%s: n_samples out of range", where);
+  if (!lon_deg || !lat_deg || !data || !pc_weights || !out)
+    return fail(CG_EINVAL, "%s: null coordinate, data, weight or output pointer", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  const int64_t n = n_samples;
+  g->index_valid = false;
+  if (n > 0) {
+    CG_CUDA(samples_keys(g, lon_deg, lat_deg, nullptr, n), where);
+    CG_CUDA(samples_sort(g, n), where);
+    CG_CUDA(samples_prepare(g, n), where);
+  } else {
+    g->last_n = 0;
+  }
+  g->index_gen += 1;
+  g->index_valid = n > 0;
+  Tiling& t = g->t64;
+  if (n > 0 && t.ranges_gen != g->index_gen) {
+    CG_CUDA(tiles_ranges(g, t), where);
+    t.ranges_gen = g->index_gen;
+  }
+  CG_CUDA(pcw_pack(g, data, data_dtype, pc_weights, n), where);
+  if (n > 0) {
+    CG_CUDA(grid_tiles_f32_to(g, g->pcw_data, CG_F32, g->pcw_acc, g->pcw_w, 0, 0.f, 2 * g->C),
+            where);
+  } else {
+    CG_CUDA(cudaMemsetAsync(g->pcw_acc, 0, sizeof(float) * (size_t)g->n_slots * 2 * g->C,
+                            g->stream),
+            where);
+  }
+  CG_CUDA(pcw_finalize(g, out, layout_channel_major ? 1 : 0, out_weights), where);
+  g->last_path = CG_PATH_FP32;
   return CG_OK;
 }
 

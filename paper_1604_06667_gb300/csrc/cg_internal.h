@@ -169,6 +169,12 @@ struct cg_grid {
   float* ds_num0 = nullptr;       // [slots][C] (w pass)
   float2* ds_w0 = nullptr;        // [slots]
   double* ds_part = nullptr;      // per-block partial sums
+  // one weight per sample and channel: [N][2C] (omega D | omega) and its
+  // [slots][2C] accumulators (cg_grid_oneshot_pcw)
+  float* pcw_data = nullptr;
+  float* pcw_acc = nullptr;
+  float2* pcw_w = nullptr;
+  size_t pcw_cap_data = 0;
 
   // candidate-split partial sums of the FP32 gridder
   float* part_num = nullptr;      // [n_split][slots][C]
@@ -241,7 +247,7 @@ int f32_default_config(int C);
 // the same into given accumulators; dscale != 0 evaluates w d^2 dscale
 // instead of w (the d/dsigma pass) and counts no pairs
 cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
-                              float2* acc_w, int accumulate, float dscale);
+                              float2* acc_w, int accumulate, float dscale, int C = -1);
 // k_grid_tc.cu -- the tile gridder, BF16 tcgen05 form (TMEM accumulators).
 // mode 0: store into the accumulators, 1: add into them, 2: one-shot
 // normalised output in the caller's [P][C] layout (out, out_w).
@@ -254,7 +260,12 @@ cudaError_t sort_samples_noalloc(int nside, const double* lon, const double* lat
 // k_finalize.cu -- normalisation and output layout.
 // k_degrid.cu -- adjoint (degridding) and d/dsigma
 cudaError_t target_index_build(cg_grid* g);
-cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* out);
+// one weight per sample and channel (k_variants.cu)
+cudaError_t pcw_pack(cg_grid* g, const void* data, int dtype, const float* omega, int64_t n);
+cudaError_t pcw_finalize(cg_grid* g, float* out, int channel_major, float* out_w);
+
+cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* out,
+                        bool interp = false, float* vsum = nullptr);
 cudaError_t grid_dsigma(cg_grid* g, const void* data, int dtype, const float* grad, float* dR,
                         double* dsigma);
 

@@ -58,6 +58,13 @@ __global__ void k_target_keys(int64_t ns, const double2* __restrict__ tll,
 
 // 1 / W per slot from a user-order weight map, or from the handle's
 // double-float accumulator (slot order); 0 where W <= 0 or not finite.
+// Normalised interpolation: every valid target slot gets the factor 1.
+__global__ void k_interp_invw(const uint32_t* __restrict__ perm, int64_t n_slots,
+                              float* __restrict__ invw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_slots) invw[i] = (perm[i] != 0xffffffffu) ? 1.f : 0.f;
+}
+
 __global__ void k_degrid_invw(const float* __restrict__ wmap, const float2* __restrict__ acc_w,
                               const uint32_t* __restrict__ perm, int64_t n_slots,
                               float* __restrict__ invw) {
@@ -110,6 +117,10 @@ struct DegridArgs {
   float* out;               // [N][C]
   int C;
   unsigned* err;
+  // normalised interpolation: coefficients w_pn (no sample weight, invw = 1),
+  // out = sum w y / sum w (NaN where no target is within r), vsum = sum w
+  int interp;
+  float* vsum;              // [N] or null
 };
 
 // One warp per 32 consecutive sorted samples; CB channels per pass (grid.y
@@ -136,6 +147,7 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
   float x[CB];
 #pragma unroll
   for (int c = 0; c < CB; ++c) x[c] = 0.f;
+  float vs = 0.f;   // sum of this sample's coefficients (interpolation)
 
   // ---- segments: runs of live samples whose neighbours (in sorted order)
   // lie within the support radius; a run that crosses into the next ring or
@@ -232,13 +244,14 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
                 const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
                 ex = fmaf(q1 * ap, ap, q2 * bp * bp) * ratio;
               }
-              coef = ex2_approx(ex) * h.w * iw;
+              coef = ex2_approx(ex) * (a.interp ? 1.f : h.w) * iw;
               if (c2 >= a.kd.c2_in) {
                 if (!pair_inside(a.tll[slot], sll, a.kd.c2r_hi, a.kd.c2r_lo, a.kd.c2r_tol,
                                  a.kd.r_rad))
                   coef = 0.f;
               }
             }
+            vs += coef;
             if (!__any_sync(0xffffffffu, coef != 0.f)) continue;
             const float* yr = a.y + (size_t)a.perm[slot] * a.C + c_base;
 #pragma unroll
@@ -251,6 +264,12 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
   }
   if (in_range) {
     float* o = a.out + (size_t)idx * a.C + c_base;
+    if (a.interp) {
+      const float inv = (vs > 0.f) ? 1.f / vs : __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int c = 0; c < CB; ++c) x[c] *= inv;
+      if (a.vsum && blockIdx.y == 0) a.vsum[idx] = vs;
+    }
 #pragma unroll
     for (int c = 0; c < CB; ++c)
       if (c_base + c < a.C) o[c] = x[c];
@@ -363,12 +382,16 @@ cudaError_t target_index_build(cg_grid* g) {
   return cudaSuccess;
 }
 
-cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* out) {
+cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* out, bool interp,
+                        float* vsum) {
   cudaStream_t s = g->stream;
   cudaError_t e = target_index_build(g);
   if (e != cudaSuccess) return e;
-  k_degrid_invw<<<ceil_div(g->n_slots, 256), 256, 0, s>>>(wmap, g->acc_w, g->tgt_perm, g->n_slots,
-                                                          g->tix_invw);
+  if (interp)
+    k_interp_invw<<<ceil_div(g->n_slots, 256), 256, 0, s>>>(g->tgt_perm, g->n_slots, g->tix_invw);
+  else
+    k_degrid_invw<<<ceil_div(g->n_slots, 256), 256, 0, s>>>(wmap, g->acc_w, g->tgt_perm,
+                                                            g->n_slots, g->tix_invw);
   g->n_launches += 1;
   DegridArgs a;
   a.ns = g->nside;
@@ -393,6 +416,8 @@ cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* ou
   a.out = out;
   a.C = g->C;
   a.err = g->d_err;
+  a.interp = interp ? 1 : 0;
+  a.vsum = vsum;
   if (a.n == 0) return cudaGetLastError();
   g->n_launches += 1;
   const bool big = g->kdev.big_support != 0;

@@ -466,7 +466,8 @@ cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype) {
 }
 
 cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
-                              float2* acc_w, int accumulate, float dscale) {
+                              float2* acc_w, int accumulate, float dscale, int C) {
+  if (C < 0) C = g->C;
   GridArgs a;
   a.tile_chi = g->t64.chi;
   a.tile_clo = g->t64.clo;
@@ -482,9 +483,9 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
   a.perm = g->sorted_val;
   a.sll = g->s_ll;
   a.data = data;
-  a.C = g->C;
+  a.C = C;
   const size_t esz = (dtype == CG_BF16) ? 2 : 4;
-  a.vec4 = (g->C % 4 == 0) && ((reinterpret_cast<uintptr_t>(data) % (4 * esz)) == 0);
+  a.vec4 = (C % 4 == 0) && ((reinterpret_cast<uintptr_t>(data) % (4 * esz)) == 0);
   a.kd = g->kdev;
   a.kd.dscale = dscale;
   a.acc_num = acc_num;
@@ -495,7 +496,7 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
   a.tile_cand = g->t64.tile_cand;
   a.n_slots = g->n_slots;
   int cfg = g->f32_cfg;
-  if (cfg < 0 || cfg >= kF32Configs) cfg = f32_default_config(g->C);
+  if (cfg < 0 || cfg >= kF32Configs || C != g->C) cfg = f32_default_config(C);
   switch (cfg) {
     case 0: return run<1, 4, 1>(g, a, dtype);
     case 1: return run<1, 8, 1>(g, a, dtype);

@@ -169,6 +169,37 @@ class Gridder:
         self.n_samples = n
         return out
 
+    def grid_oneshot_pcw(self, lon, lat, data, pc_weights, out=None, out_weights=None,
+                         channel_major: bool = False):
+        """Eq. 1-3 with one weight per sample and channel (cg_grid_oneshot_pcw):
+        pc_weights [N, C] float32 >= 0.  Returns the map; out_weights (same
+        shape as the map) receives W_pc."""
+        lon, lat, data, _, n = self._prep(lon, lat, data, None)
+        pcw = torch.as_tensor(pc_weights, device=self.device, dtype=torch.float32)
+        pcw = pcw.reshape(n, self.n_channels).contiguous()
+        shape = (self.n_channels, self.n_targets) if channel_major else \
+            (self.n_targets, self.n_channels)
+        if out is None:
+            out = torch.empty(shape, device=self.device, dtype=torch.float32)
+        C.cg_grid_oneshot_pcw(self._h, _ptr(lon), _ptr(lat), _ptr(data), self._data_dtype(data),
+                              _ptr(pcw), n, _ptr(out), 1 if channel_major else 0,
+                              _ptr(out_weights))
+        self._keep = (lon, lat, data, pcw)
+        return out
+
+    def interp(self, ymap, out=None, out_weights=None):
+        """Normalised interpolation of ymap [P, C] at the samples of the last
+        add (cg_interp): out[n] = sum_p w_pn y_p / sum_p w_pn, NaN where no
+        target is within the support; out_weights [N] receives the sums."""
+        y = torch.as_tensor(ymap, device=self.device, dtype=torch.float32)
+        y = y.reshape(self.n_targets, self.n_channels).contiguous()
+        n = int(self.n_samples)
+        if out is None:
+            out = torch.empty((n, self.n_channels), device=self.device, dtype=torch.float32)
+        C.cg_interp(self._h, _ptr(y), _ptr(out), _ptr(out_weights), n)
+        self._keep_map = y
+        return out
+
     # -- adjoint and kernel-width derivative ------------------------------
     def degrid(self, ymap, map_weights=None, out=None):
         """G^T y: the adjoint of the normalised gridding of the last add's

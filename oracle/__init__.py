@@ -52,6 +52,12 @@ def gauss2d(smaj_deg: float, smin_deg: float, pa_deg: float, support_deg: float)
     return Kernel(1, 0.0, smaj_deg, smin_deg, pa_deg, support_deg)
 
 
+def tapered_sinc(a_deg: float, b_deg: float, support_deg: float) -> Kernel:
+    """w(d) = sin(pi d / a) / (pi d / a) * exp(-d^2 / b^2): the sin(x)/x kernel
+    the paper names (App. A.1), tapered so that a finite support suffices."""
+    return Kernel(2, b_deg, a_deg, 0.0, 0.0, support_deg)
+
+
 def lib():
     global _lib
     if _lib is None:

@@ -258,9 +258,9 @@ double or_bearing(double lon1_deg, double lat1_deg, double lon2_deg, double lat2
 }
 
 typedef struct {
-  int32_t type;         /* 0 = gauss1d, 1 = elliptical gauss2d */
-  double sigma_deg;     /* gauss1d */
-  double smaj_deg;      /* gauss2d major-axis sigma */
+  int32_t type;         /* 0 = gauss1d, 1 = elliptical gauss2d, 2 = tapered sinc */
+  double sigma_deg;     /* gauss1d; tapered sinc: taper width b */
+  double smaj_deg;      /* gauss2d major-axis sigma; tapered sinc: first zero a */
   double smin_deg;      /* gauss2d minor-axis sigma */
   double pa_deg;        /* gauss2d position angle of the major axis, N through E */
   double support_deg;   /* support radius r */
@@ -278,6 +278,13 @@ static double kernel_eval(const or_kernel* k, double lt, double bt, double ls, d
   if (k->type == 0) {
     const double s = k->sigma_deg * OR_DEG2RAD;
     return exp(-(d * d) / (2.0 * s * s));
+  } else if (k->type == 2) {
+    /* the sin(x)/x kernel of App. A.1, x = pi d / a, tapered by
+     * exp(-d^2 / b^2) so that a finite support suffices */
+    const double a = k->smaj_deg * OR_DEG2RAD, b = k->sigma_deg * OR_DEG2RAD;
+    const double x = OR_PI * d / a;
+    const double sinc = (x == 0.0) ? 1.0 : sin(x) / x;
+    return sinc * exp(-(d * d) / (b * b));
   } else {
     const double beta = or_bearing(lt, bt, ls, bs);
     const double pa = k->pa_deg * OR_DEG2RAD;
@@ -339,7 +346,7 @@ int or_grid_bruteforce(int64_t P, const double* lon_t, const double* lat_t, int6
       acc_add(&aw[p], ww);
       for (int32_t c = 0; c < C; ++c) {
         acc_add(&anum[p * C + c], ww * data[n * C + c]);
-        acc_add(&aabs[p * C + c], ww * fabs(data[n * C + c]));
+        acc_add(&aabs[p * C + c], fabs(ww * data[n * C + c]));
       }
     }
   }
@@ -586,7 +593,7 @@ int or_grid_lookup(int64_t ns, int32_t mode, int64_t P, const double* lon_t,
         acc_add(&aw[t], ww);
         for (int32_t c = 0; c < C; ++c) {
           acc_add(&anum[t * C + c], ww * data[n * C + c]);
-          acc_add(&aabs[t * C + c], ww * fabs(data[n * C + c]));
+          acc_add(&aabs[t * C + c], fabs(ww * data[n * C + c]));
         }
       }
     }

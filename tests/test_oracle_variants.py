@@ -84,3 +84,35 @@ def test_pcw_scaling_and_independence():
     assert np.allclose(R2[on, 1], R[on, 1], rtol=1e-12, atol=1e-13)
     assert np.allclose(W2[on, 1], 4.0 * W[on, 1], rtol=1e-13, atol=0)
     assert np.array_equal(R2[:, 0], R[:, 0], equal_nan=True)
+
+
+def test_tapered_sinc_closed_forms():
+    """sin(x)/x at x = pi d / a, taper exp(-d^2 / b^2): zeros at d = a, 2a;
+    1 at d = 0; 2/pi at d = a / 2 and -2/(3 pi) at d = 3a/2 (times the
+    taper); evaluated for a target at (0, 0) and samples on the equator."""
+    a, b = 0.2, 0.35
+    k = oracle.tapered_sinc(a, b, 1.0)
+    L = oracle.lib()
+    val = lambda d: L.or_kernel_value(k, 0.0, 0.0, d, 0.0)
+    assert val(0.0) == 1.0
+    assert abs(val(a)) < 1e-15 and abs(val(2 * a)) < 1e-15
+    assert math.isclose(val(a / 2), (2 / math.pi) * math.exp(-(a / 2 / b) ** 2), rel_tol=1e-12)
+    assert math.isclose(val(1.5 * a), (-2 / (3 * math.pi)) * math.exp(-(1.5 * a / b) ** 2),
+                        rel_tol=1e-12)
+    assert val(1.01) == 0.0                      # beyond the support
+
+
+def test_tapered_sinc_single_sample():
+    """One sample: R = D wherever its (signed) weight is positive; where the
+    weight map is negative (the sinc's negative lobe) R is NaN (W > 0 rule)."""
+    a, b = 0.2, 0.5
+    k = oracle.tapered_sinc(a, b, 0.6)
+    lon_t = np.linspace(-0.55, 0.55, 45)
+    lat_t = np.zeros_like(lon_t)
+    res = oracle.grid_bruteforce(lon_t, lat_t, [0.0], [0.0], [[2.5]], k)
+    d = np.abs(lon_t)
+    pos = np.sin(np.pi * d / a) / np.where(d > 0, np.pi * d / a, 1.0)
+    pos = np.where(d > 0, pos, 1.0) > 1e-9
+    assert np.allclose(res.out[pos, 0], 2.5, rtol=1e-13)
+    neg = (res.wsum < 0)
+    assert neg.any() and np.all(np.isnan(res.out[neg, 0]))

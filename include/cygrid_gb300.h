@@ -61,11 +61,14 @@ typedef enum { CG_F32 = 0, CG_BF16 = 1 } cg_dtype;
 
 typedef enum {
   CG_GAUSS1D = 0, /* params[0] = sigma (deg): w = exp(-d^2 / (2 sigma^2)) */
-  CG_GAUSS2D = 1  /* params = {sigma_maj, sigma_min, PA} (deg), PA of the
+  CG_GAUSS2D = 1, /* params = {sigma_maj, sigma_min, PA} (deg), PA of the
                      major axis from north through east; with beta the
                      bearing of the sample seen from the target,
                      a = d cos(beta - PA), b = d sin(beta - PA),
                      w = exp(-a^2/(2 sigma_maj^2) - b^2/(2 sigma_min^2)) */
+  CG_TSINC = 2    /* params = {a, b} (deg): the sin(x)/x kernel tapered by a
+                     Gaussian, w = sin(pi d/a) / (pi d/a) exp(-d^2 / b^2);
+                     weights can be negative, and R is NaN where W <= 0 */
 } cg_kernel;
 
 typedef enum {
@@ -97,7 +100,8 @@ cg_status cg_grid_create(cg_grid** out, const double* lon_deg, const double* lat
 
 /* Set the kernel (paper Sect. 3.5, set_kernel).
  *   kernel_type   cg_kernel.
- *   params        host, [n_params]: {sigma} or {sigma_maj, sigma_min, PA}, degrees.
+ *   params        host, [n_params]: {sigma}, {sigma_maj, sigma_min, PA} or {a, b},
+ *                 degrees.
  *   support_deg   support radius r > 0: samples with d > r do not contribute.
  *   nside         internal HEALPix resolution (power of two, 1 .. 8192), or 0 to
  *                 derive it from hpx_maxres_deg: the smallest power of two with

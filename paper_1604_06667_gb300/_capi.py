@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libcygrid_gb300.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_EDEVICE, CG_ETIMEOUT, CG_ESTATE = range(7)
 CG_F32, CG_BF16 = 0, 1
-CG_GAUSS1D, CG_GAUSS2D = 0, 1
+CG_GAUSS1D, CG_GAUSS2D, CG_TSINC = 0, 1, 2
 CG_PATH_AUTO, CG_PATH_FP32, CG_PATH_TC, CG_PATH_TC_FAST = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_EDEVICE",

@@ -365,6 +365,10 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
     sig1 = params[0];
     sig2 = params[1];
     pa = params[2];
+  } else if (kernel_type == CG_TSINC) {
+    if (n_params < 2 || !finite_pos(params[0]) || !finite_pos(params[1]))
+      return fail(CG_EINVAL, "cg_set_kernel: tsinc needs params = {a > 0, b > 0}");
+    sig1 = sig2 = params[1];
   } else {
     return fail(CG_EINVAL, "cg_set_kernel: unknown kernel type %d", kernel_type);
   }
@@ -384,7 +388,7 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
   CG_CUDA(cudaSetDevice(g->device), "cg_set_kernel");
   g->kernel_type = kernel_type;
   g->kparams[0] = params[0];
-  g->kparams[1] = (kernel_type == CG_GAUSS2D) ? params[1] : 0.0;
+  g->kparams[1] = (kernel_type == CG_GAUSS2D || kernel_type == CG_TSINC) ? params[1] : 0.0;
   g->kparams[2] = (kernel_type == CG_GAUSS2D) ? params[2] : 0.0;
   g->support_deg = support_deg;
   g->nside = ns;
@@ -394,6 +398,10 @@ cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params, i
   const double s1 = sig1 * kDeg2Rad, s2 = sig2 * kDeg2Rad;
   kd.k1 = (float)(-log2e / (2.0 * s1 * s1));
   kd.k2 = (float)(-log2e / (2.0 * s2 * s2));
+  if (kernel_type == CG_TSINC) {   // taper exp(-d^2 / b^2), zeros of the sinc at d = a, 2a, ...
+    kd.k1 = (float)(-log2e / (s1 * s1));
+    kd.inv_a = (float)(1.0 / (params[0] * kDeg2Rad));
+  }
   const double r = support_deg * kDeg2Rad;
   const double chord = 2.0 * std::sin(0.5 * std::fmin(r, kPi));
   kd.r_rad = r;

@@ -29,6 +29,11 @@ __device__ __forceinline__ void set_error(unsigned* err, unsigned bit) {
   if (err) atomicOr(err, bit);
 }
 
+// sin(pi x) / (pi x), 1 at x = 0 (the tapered-sinc kernel's sinc factor)
+__device__ __forceinline__ float sinc_pi(float x) {
+  return (x == 0.f) ? 1.f : sinpif(x) / (3.14159265358979f * x);
+}
+
 // ---------------------------------------------------------------------------
 // HEALPix RING index in FP64 (Gorski et al. 2005; the paper's Sect. 2.2
 // step 3a).  The operation sequence is fixed with explicit round-to-nearest

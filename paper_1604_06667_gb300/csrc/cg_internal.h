@@ -39,6 +39,7 @@ struct KernelDev {        // kernel constants used by the gridder
   float c2r_tol;          // tolerance of the double-float squared chord of a pair
   int big_support;        // 1 if the chord series for d^2 is not accurate enough
   float dscale;           // 0; else the weight is w d^2 dscale (d/dsigma pass)
+  float inv_a;            // CG_TSINC: 1 / a (rad^-1); k1 then holds the taper -log2(e)/b^2
 };
 
 struct Tiling {           // geometry of one tiling of the targets

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
                 d2 = d * d;
               }
               float ex;
-              if (KT == CG_GAUSS1D) {
+              if (KT == CG_GAUSS1D || KT == CG_TSINC) {
                 ex = q1 * d2;
               } else {
                 const float4 f1 = a.f1[slot], f2 = a.f2[slot];
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256) k_degrid(DegridArgs a) {
                 ex = fmaf(q1 * ap, ap, q2 * bp * bp) * ratio;
               }
               coef = ex2_approx(ex) * (a.interp ? 1.f : h.w) * iw;
+              if (KT == CG_TSINC) coef *= sinc_pi(sqrtf(d2) * a.kd.inv_a);
               if (c2 >= a.kd.c2_in) {
                 if (!pair_inside(a.tll[slot], sll, a.kd.c2r_hi, a.kd.c2r_lo, a.kd.c2r_tol,
                                  a.kd.r_rad))
@@ -283,6 +284,8 @@ cudaError_t launch_degrid(const DegridArgs& a, bool big, cudaStream_t s) {
   if (a.kd.type == CG_GAUSS1D) {
     if (big) k_degrid<CB, CG_GAUSS1D, true><<<grid, 256, 0, s>>>(a);
     else k_degrid<CB, CG_GAUSS1D, false><<<grid, 256, 0, s>>>(a);
+  } else if (a.kd.type == CG_TSINC) {
+    k_degrid<CB, CG_TSINC, true><<<grid, 256, 0, s>>>(a);
   } else {
     if (big) k_degrid<CB, CG_GAUSS2D, true><<<grid, 256, 0, s>>>(a);
     else k_degrid<CB, CG_GAUSS2D, false><<<grid, 256, 0, s>>>(a);

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
             d2 = d * d;
           }
           float ex;
-          if (a.kd.type == CG_GAUSS1D) {
+          if (a.kd.type == CG_GAUSS1D || a.kd.type == CG_TSINC) {
             ex = a.kd.k1 * d2;
           } else {
             const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
@@ -255,15 +255,16 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
             ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
           }
           w = ex2_approx(ex) * sh.w;
+          if (a.kd.type == CG_TSINC) w *= sinc_pi(sqrtf(d2) * a.kd.inv_a);
           if (a.kd.dscale != 0.f) w *= d2 * a.kd.dscale;   // dw/dsigma pass
+          bool in = true;
           if (c2 >= a.kd.c2_in) {
             // guard band: decide d <= r again from the input coordinates
             const uint32_t idx = sh_idx[k];
-            if (!pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
-                                 a.kd.c2r_tol, a.kd.r_rad))
-              w = -1.f;
+            in = pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
+                                 a.kd.c2r_tol, a.kd.r_rad);
           }
-          if (w >= 0.f) ++npair; else w = 0.f;
+          if (in) ++npair; else w = 0.f;
         }
         w_s[k][p] = w;
         // Neumaier (two-sum) accumulation of the weight map

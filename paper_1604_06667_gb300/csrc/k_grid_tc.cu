@@ -310,6 +310,7 @@ struct PairConst {
   float2 mid2;               // (mid, mid)
   float mid, hw;             // band centre and half-width (chord^2)
   float e_mid;
+  float inv_a;               // CG_TSINC: 1 / a (rad^-1)
 };
 
 template <int KT, bool BIG>
@@ -328,6 +329,7 @@ __device__ __forceinline__ PairConst make_pair_const(const KernelDev& kd) {
   P.q1 = make_float2(kd.k1, kd.k1);
   P.q4 = make_float2(kd.k2, kd.k2);
   P.e_mid = series ? (float)(q1 * m + q2 * m * m) : 0.f;
+  P.inv_a = kd.inv_a;
   return P;
 }
 
@@ -383,7 +385,14 @@ __device__ __forceinline__ void eval_group(const float* cand, const uint32_t* ci
     const float2 x = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, P.nmid)));
     const float2 lw = make_float2(zl.z, zl.w);
     float2 e;
-    if (BIG) {
+    float2 sf = make_float2(1.f, 1.f);   // the tapered sinc's sinc factor
+    if (KT == CG_TSINC) {
+      const float2 c2 = __fadd2_rn(x, P.mid2);
+      const float d0 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(fmaxf(c2.x, 0.f))));
+      const float d1 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(fmaxf(c2.y, 0.f))));
+      e = __ffma2_rn(P.q1, make_float2(d0 * d0, d1 * d1), lw);
+      sf = make_float2(sinc_pi(d0 * P.inv_a), sinc_pi(d1 * P.inv_a));
+    } else if (BIG) {
       const float2 c2 = __fadd2_rn(x, P.mid2);
       const float d0 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2.x)));
       const float d1 = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2.y)));
@@ -413,8 +422,8 @@ __device__ __forceinline__ void eval_group(const float* cand, const uint32_t* ci
       e = __ffma2_rn(t, ratio, lw);
     }
     const bool in0 = x.x <= P.hw, in1 = x.y <= P.hw;
-    w[2 * j] = in0 ? ex2_approx(e.x) : 0.f;
-    w[2 * j + 1] = in1 ? ex2_approx(e.y) : 0.f;
+    w[2 * j] = in0 ? ex2_approx(e.x) * sf.x : 0.f;
+    w[2 * j + 1] = in1 ? ex2_approx(e.y) * sf.y : 0.f;
     np += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
     bm = fminf(bm, fminf(fabsf(x.x), fabsf(x.y)));
   }
@@ -973,6 +982,8 @@ __global__ void __launch_bounds__(kOrderThreads) k_item_order(const int32_t* __r
 
 using KernFn = void (*)(const CUtensorMap, TcArgs);
 KernFn pick_kernel(int kt, bool split, bool big) {
+  if (kt == CG_TSINC)
+    return split ? k_grid_tc<CG_TSINC, true, true> : k_grid_tc<CG_TSINC, false, true>;
   if (kt == CG_GAUSS1D) {
     if (big) return split ? k_grid_tc<CG_GAUSS1D, true, true> : k_grid_tc<CG_GAUSS1D, false, true>;
     return split ? k_grid_tc<CG_GAUSS1D, true, false> : k_grid_tc<CG_GAUSS1D, false, false>;

@@ -16,7 +16,7 @@ import torch
 
 from . import _capi as C
 
-_KERNELS = {"gauss1d": C.CG_GAUSS1D, "gauss2d": C.CG_GAUSS2D}
+_KERNELS = {"gauss1d": C.CG_GAUSS1D, "gauss2d": C.CG_GAUSS2D, "tsinc": C.CG_TSINC}
 
 
 def _ptr(t):

@@ -209,6 +209,55 @@ __device__ __forceinline__ int64_t ang2pix_ring_fast(int64_t ns, double lon_deg,
   return pix;
 }
 
+// floor of a double-float and its fractional part (as FP32).
+__device__ __forceinline__ float df_floor(df32 a, float& frac) {
+  float f = floorf(a.hi);
+  if (f == a.hi && a.lo < 0.f) f -= 1.f;   // a sits just below the integer a.hi
+  frac = (a.hi - f) + a.lo;                 // a.hi - f is exact
+  return f;
+}
+
+// The belt part of ang2pix_ring_fast in double-float arithmetic (no FP64
+// operations): longitude lon (degrees, double-float, folded here), z = sin
+// lat as a double-float (|error| ~1e-14).  *ok = false outside the belt
+// (|z| >= 2/3 - 1e-9) or when a truncated quantity lies within the 1e-6
+// margin of an integer (df32 evaluates them to ~2^-48 relative, so the
+// decisions outside the margin are those of the FP64 definition).
+__device__ __forceinline__ int64_t ang2pix_ring_belt_df(int64_t ns, df32 lon, df32 z, bool* ok) {
+  constexpr float M = 1e-6f;
+  const float za = fabsf(z.hi);
+  if (!(za < (float)(2.0 / 3.0) - 1e-6f) || ns > 16384) {
+    *ok = false;
+    return 0;
+  }
+  // phi in [0, 360): fold by whole turns (exact in FP32 for |lon| < 2^24)
+  if (lon.hi < 0.f || lon.hi >= 360.f) {
+    const float k = floorf(lon.hi * (1.f / 360.f));
+    lon = df_add(lon, df32{-360.f * k, 0.f});
+    if (lon.hi < 0.f) lon = df_add(lon, df32{360.f, 0.f});
+    if (lon.hi >= 360.f) lon = df_add(lon, df32{-360.f, 0.f});
+  }
+  constexpr double kInv90 = 1.0 / 90.0;
+  const df32 tt = df_mul(lon, df32{(float)kInv90, (float)(kInv90 - (double)(float)kInv90)});
+  const float dns = (float)ns;                           // a power of two or exact integer
+  df32 u = df_add(tt, df32{0.5f, 0.f});
+  u = df32{u.hi * dns, u.lo * dns};
+  const df32 v = df_mul(z, df32{0.75f * dns, 0.f});
+  const df32 A = df_add(u, df_neg(v)), B = df_add(u, v);
+  float fa, fb;
+  const float Af = df_floor(A, fa), Bf = df_floor(B, fb);
+  *ok = fa > M && fa < 1.f - M && fb > M && fb < 1.f - M;
+  const int64_t asc = (int64_t)Af;
+  const int64_t dsc = (int64_t)Bf;
+  int64_t k = ns + 1 + asc - dsc;
+  k = k < 1 ? 1 : (k > 2 * ns + 1 ? 2 * ns + 1 : k);
+  const int64_t odd = k & 1;
+  int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
+  j %= 4 * ns;
+  if (j < 0) j += 4 * ns;
+  return 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
+}
+
 // RING index of a valid sample with z from the double-float sine; exact
 // FP64 fallback near decision boundaries.
 __device__ __forceinline__ int64_t ang2pix_ring_dual(int64_t ns, double lon, double lat,

@@ -118,4 +118,58 @@ __device__ __forceinline__ void df_sincos_deg(double a, df32& s, df32& c) {
   }
 }
 
+// ---- the same without FP64 arithmetic -------------------------------------
+// GB300 executes FP64 (and FP64 <-> FP32 conversions) at a few operations per
+// SM and clock, so the per-sample path splits its FP64 inputs with integer
+// operations and reduces the argument in double-float.
+
+// a as hi + lo: hi = a truncated to 24 significant bits, lo = the remainder
+// rounded to FP32 (|error| <= 2^-48 |a|).  Valid for 2^-100 <= |a| < 2^100 or
+// a = 0 (df_split_ok tells).
+__device__ __forceinline__ bool df_split_ok(double a) {
+  const int e = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
+  return e == 0 ? a == 0.0 : (e >= 1023 - 100 && e < 1023 + 100);
+}
+__device__ __forceinline__ df32 df_split(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return df32{0.f, 0.f};
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  // remainder: the low 29 mantissa bits, worth 2^(e - 1075) each
+  const float r = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull));
+  const float scale = __uint_as_float((unsigned)(e - 1023 - 23 + 127) << 23);   // 2^(e-1046)
+  const float lo = r * 1.86264514923095703125e-9f * scale;                       // r 2^-29 2^(e-1046)
+  return df32{hi, sign ? -lo : lo};
+}
+
+// sin and cos of a (degrees, double-float, |a| < 2^17): as df_sincos_deg with
+// the reduction a = r + 90 n done in double-float (90 n is exact in FP32).
+__device__ __forceinline__ void df_sincos_deg_df(df32 a, df32& s, df32& c) {
+  const float qd = rintf(a.hi * (1.f / 90.f));
+  const df32 r = df_add(a, df32{-90.f * qd, 0.f});    // |r| <= 45 deg (+ rounding)
+  const int n = (int)qd & 3;
+  const df32 x = df_mul(r, df32{kD2R_hi, kD2R_lo});
+  const int j = __float2int_rn(x.hi * 64.f);
+  const int ja = j < 0 ? -j : j;
+  const float4 tab = *reinterpret_cast<const float4*>(&kTrigTable.v[4 * ja]);
+  const df32 S = (j < 0) ? df32{-tab.x, -tab.y} : df32{tab.x, tab.y};
+  const df32 C = df32{tab.z, tab.w};
+  const df32 t = df_two_sum(x.hi - (float)j * (1.f / 64.f), x.lo);
+  const df32 t2 = df_two_prod(t.hi, t.hi);
+  const float t2lo = fmaf(2.f * t.hi, t.lo, t2.lo);
+  const df32 u = df_fast_two_sum(0.5f * t2.hi, fmaf(-t2.hi * (1.f / 24.f), t2.hi, 0.5f * t2lo));
+  const float v = t2.hi * fmaf(-t2.hi, 1.f / 120.f, 1.f / 6.f);
+  const df32 st = df_add(t, df32{-t.hi * v, -t.lo * v});
+  const df32 sx = df_add(df_add(S, df_neg(df_mul(S, u))), df_mul(C, st));
+  const df32 cx = df_add(df_add(C, df_neg(df_mul(C, u))), df_neg(df_mul(S, st)));
+  switch (n) {
+    case 0: s = sx; c = cx; break;
+    case 1: s = cx; c = df_neg(sx); break;
+    case 2: s = df_neg(sx); c = df_neg(cx); break;
+    default: s = df_neg(cx); c = sx; break;
+  }
+}
+
 }  // namespace cg

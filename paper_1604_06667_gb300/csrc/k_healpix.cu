@@ -90,6 +90,30 @@ __global__ void __launch_bounds__(32 * kQueryWarps) k_tile_query(
 }
 
 
+// RING index of a valid direction and the double-float sine / cosine of its
+// latitude and longitude.  Ordinary angles (|lon| < 2048 deg) take an FP64-free
+// path: the inputs are split into double-float pairs with integer operations,
+// the trigonometry and the belt's index arithmetic run in double-float, and
+// only a decision within the margin of a pixel boundary, the polar caps and
+// the cap/belt boundary go to the FP64 routines.
+__device__ __forceinline__ int64_t key_and_sincos(int64_t ns, double lo, double la, df32& sb,
+                                                  df32& cb, df32& sl, df32& cl) {
+  const bool fast = df_split_ok(lo) && df_split_ok(la) &&
+                    (__double_as_longlong(lo) & 0x7ff0000000000000ll) < (1034ll << 52);
+  bool ok = false;
+  int64_t kpix = 0;
+  if (fast) {
+    const df32 lon_d = df_split(lo), lat_d = df_split(la);
+    df_sincos_deg_df(lat_d, sb, cb);
+    df_sincos_deg_df(lon_d, sl, cl);
+    kpix = ang2pix_ring_belt_df(ns, lon_d, sb, &ok);
+  } else {
+    df_sincos_deg(la, sb, cb);
+    df_sincos_deg(lo, sl, cl);
+  }
+  return ok ? kpix : ang2pix_ring_dual(ns, lo, la, sb);
+}
+
 __global__ void k_ang2pix_export(int64_t ns, const double* __restrict__ lon,
                                  const double* __restrict__ lat, int64_t n,
                                  int64_t* __restrict__ pix) {
@@ -100,9 +124,8 @@ __global__ void k_ang2pix_export(int64_t ns, const double* __restrict__ lon,
     pix[i] = -1;
     return;
   }
-  df32 sb, cb;
-  df_sincos_deg(la, sb, cb);
-  pix[i] = ang2pix_ring_dual(ns, lo, la, sb);
+  df32 sb, cb, sl, cl;
+  pix[i] = key_and_sincos(ns, lo, la, sb, cb, sl, cl);
 }
 
 // Unit vectors (double-float) of n directions, as FP64 [n][3].
@@ -141,9 +164,7 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
     return;
   }
   df32 sb, cb, sl, cl;
-  df_sincos_deg(la, sb, cb);
-  df_sincos_deg(lo, sl, cl);
-  key[i] = (uint32_t)ang2pix_ring_dual(ns, lo, la, sb);
+  key[i] = (uint32_t)key_and_sincos(ns, lo, la, sb, cb, sl, cl);
   const df32 x = df_mul(cb, cl), y = df_mul(cb, sl);
   float w = 1.f;
   if (weights) {

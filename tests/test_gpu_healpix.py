@@ -56,6 +56,38 @@ def test_ang2pix_bit_exact(ns):
     assert bad.size <= 2
 
 
+@pytest.mark.parametrize("ns", [16, 1024, 4096, 8192])
+def test_sample_keys_bit_exact(ns):
+    """The gridder's own per-sample keys (the double-float path for ordinary
+    angles, FP64 near boundaries, in the poles' caps and for |lon| >= 2048)
+    sorted and exported: equal to the oracle's sort of its keys."""
+    import torch
+    from paper_1604_06667_gb300 import Gridder
+    rng = np.random.Generator(np.random.PCG64(200 + ns))
+    n = 300_000
+    lon = np.concatenate([rng.uniform(-720, 720, n), rng.uniform(-5000, 5000, 2000)])
+    lat = np.degrees(np.arcsin(rng.uniform(-1, 1, lon.size)))
+    al, ab = adversarial(ns, rng)
+    lon = np.concatenate([lon, al])
+    lat = np.concatenate([lat, ab])
+    g = Gridder(np.array([0.0]), np.array([0.0]), n_channels=1)
+    sigma = math.degrees(math.sqrt(math.pi / 3) / ns)
+    g.set_kernel("gauss1d", (sigma,), 3 * sigma, nside=ns)
+    g.grid(lon, lat, torch.zeros((lon.size, 1)))
+    pix, perm, _ = g.export_index(lon.size)
+    g.sync()
+    pix, perm = pix.cpu().numpy(), perm.cpu().numpy()
+    g.close()
+    got = np.empty_like(pix)
+    got[perm] = pix
+    ref = oracle.ang2pix(ns, lon, lat)
+    bad = np.nonzero(got != ref)[0]
+    if bad.size:
+        margins = oracle.ang2pix_margin(ns, lon[bad], lat[bad])
+        assert np.all(margins < 1e-9), (bad[:5], got[bad[:5]], ref[bad[:5]], margins[:5])
+    assert bad.size <= 2
+
+
 def test_ang2pix_invalid_inputs():
     from paper_1604_06667_gb300 import ang2pix_ring
     lon = np.array([0.0, np.nan, 10.0, np.inf, 10.0, 5.0])

@@ -283,6 +283,10 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
                 "kernel": "k_grid_tc (tile gridder, BF16 tcgen05 + TMEM)",
                 "bytes_per_launch": kbytes, "peak_source": peaks_src,
                 "tensor_useful_tflops": 2.0 * upd / (t_grid / 1e3) / 1e12,
+                # MMA work as executed: every evaluated (target, candidate)
+                # weight times C channels, hi + lo BF16 halves
+                "tensor_executed_tflops": 2.0 * 2.0 * C * float(info1["n_candidates"]) *
+                float(info1["tile_size"]) / (t_grid / 1e3) / 1e12,
                 "tensor_peak_tflops": peaks.get("bf16_tflops")}
     step_bytes = algorithmic_bytes(wl, dbytes)
     return {
@@ -359,8 +363,8 @@ def time_differentiable(args, dev):
 # ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (summary under
 # profiles/); valid only for the kernel source it was taken with.
 TRAFFIC_CAPTURE = {"source": "paper_1604_06667_gb300/csrc/k_grid_tc.cu",
-                   "sha256": "d1d58f8e04b0a54fc1cf9da6324a68f4f51e5bf7dbcf07ede01e8219f066836b",
-                   "bytes_per_launch": 910251520 + 257925632}
+                   "sha256": "6d288cefe4dc1a2510d3a314a90da626f2b58194352a8f6ca61e3f0976f38380",
+                   "bytes_per_launch": 2238623488 + 260987904}
 
 
 def captured_traffic():

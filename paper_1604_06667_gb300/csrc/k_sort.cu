@@ -250,43 +250,70 @@ __device__ __forceinline__ uint64_t os_word(uint32_t epoch, uint64_t kind, uint3
   return ((uint64_t)epoch << 34) | (kind << 32) | v;
 }
 
+// One pass.  Warp w of the tile ranks the keys [512 w, 512 w + 512) of the
+// tile, 32 consecutive keys per round: equal digits of a round are grouped by
+// a warp match, the warp's running count per digit lives in its own row of
+// shared counters, so ranking needs no block barrier.  Then one block step
+// turns the per-warp counts into per-warp digit offsets and the tile's digit
+// counts, the look-back finds the tile's offsets, and every key is written
+// to  tile offset + offset of its warp + its rank within the warp  -- the
+// position of the key among equal digits follows its input position (stable).
 __global__ void __launch_bounds__(kThreads) k_os_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
     const uint32_t* __restrict__ ghist, uint64_t* status, uint32_t* ticket, uint32_t epoch,
     unsigned* err) {
+  constexpr int kPerWarp = kOsTile / kWarps;       // 512 keys per warp
   __shared__ uint32_t s_b;
   __shared__ uint32_t blk_off[kRadix];
-  __shared__ uint32_t cnt[kRadix];
   __shared__ uint32_t wcnt[kWarps][kRadix];
-  __shared__ uint32_t run[kRadix];
   __shared__ uint32_t warp_sums[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_b = atomicAdd(ticket, 1u);
-  cnt[tid] = 0;
-  run[tid] = 0;
+#pragma unroll
+  for (int w2 = 0; w2 < kWarps; ++w2) wcnt[w2][tid] = 0;
   __syncthreads();
   const int64_t b = s_b;
-  const int64_t base = b * kOsTile;
-  // this tile's digit counts
-  uint32_t k_it[kOsItems], v_it[kOsItems];
+  const int64_t wbase = b * kOsTile + (int64_t)wid * kPerWarp;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t k_it[kOsItems], v_it[kOsItems], r_it[kOsItems];
 #pragma unroll
   for (int it = 0; it < kOsItems; ++it) {
-    const int64_t i = base + (int64_t)it * kThreads + tid;
+    const int64_t i = wbase + it * 32 + lane;
     k_it[it] = 0;
     v_it[it] = 0;
     if (i < n) {
       k_it[it] = kin[i];
       v_it[it] = vin[i];
-      atomicAdd(&cnt[(k_it[it] >> shift) & 0xffu], 1u);
     }
   }
+  // ranks within the warp, round by round
+  uint32_t* wc = wcnt[wid];
+#pragma unroll
+  for (int it = 0; it < kOsItems; ++it) {
+    const bool valid = wbase + it * 32 + lane < n;
+    const unsigned d = valid ? ((k_it[it] >> shift) & 0xffu) : (unsigned)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt_mask);
+    const uint32_t c0 = valid ? wc[d] : 0u;
+    r_it[it] = c0 + before;
+    __syncwarp();
+    if (valid && before == 0) wc[d] = c0 + __popc(peers);
+    __syncwarp();
+  }
   __syncthreads();
+  // digit tid: offsets of the warps within the tile, and the tile's count
+  uint32_t c = 0;
+#pragma unroll
+  for (int w2 = 0; w2 < kWarps; ++w2) {
+    const uint32_t x = wcnt[w2][tid];
+    wcnt[w2][tid] = c;
+    c += x;
+  }
   // global exclusive offset of digit tid
   uint32_t tot;
   const uint32_t g_excl = block_exclusive_scan(ghist[tid], warp_sums, tot);
   // publish the count, look back for the prefix, publish the prefix
-  const uint32_t c = cnt[tid];
   volatile uint64_t* st = status;
   if (b == 0) {
     st[(size_t)tid] = os_word(epoch, kInc, c);
@@ -329,37 +356,14 @@ __global__ void __launch_bounds__(kThreads) k_os_pass(
     blk_off[tid] = g_excl + prefix;
   }
   __syncthreads();
-  // stable ranks in (item, thread) order and scatter
-  const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int it = 0; it < kOsItems; ++it) {
-    const int64_t i = base + (int64_t)it * kThreads + tid;
-    const bool valid = i < n;
-    const unsigned d = valid ? ((k_it[it] >> shift) & 0xffu) : (unsigned)kRadix;
-#pragma unroll
-    for (int w2 = 0; w2 < kWarps; ++w2) wcnt[w2][tid] = 0;
-    __syncthreads();
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t r = run[tid];
-#pragma unroll
-      for (int w2 = 0; w2 < kWarps; ++w2) {
-        const uint32_t cc = wcnt[w2][tid];
-        wcnt[w2][tid] = r;
-        r += cc;
-      }
-      run[tid] = r;
-    }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = blk_off[d] + wcnt[wid][d] + rank;
+    if (wbase + it * 32 + lane < n) {
+      const unsigned d = (k_it[it] >> shift) & 0xffu;
+      const uint32_t pos = blk_off[d] + wc[d] + r_it[it];
       kout[pos] = k_it[it];
       vout[pos] = v_it[it];
     }
-    __syncthreads();   // wcnt is cleared for the next item
   }
 }
 

@@ -97,7 +97,7 @@ def test_ang2pix_invalid_inputs():
     assert np.all(got[1:] == -1)
 
 
-@pytest.mark.parametrize("case", ["cube", "allsky", "dup"])
+@pytest.mark.parametrize("case", ["cube", "allsky", "dup", "dup_many_tiles"])
 def test_sort_and_ring_offsets_bit_exact(case):
     import torch
     from paper_1604_06667_gb300 import Gridder
@@ -106,9 +106,10 @@ def test_sort_and_ring_offsets_bit_exact(case):
     elif case == "allsky":
         wl = workloads.allsky(scale=0.01, n_channels=2)
     else:
-        # many exact duplicates: ties must keep ascending sample order
-        base = workloads.plain2d(scale=0.05)
-        rep = 7
+        # many exact duplicates: ties must keep ascending sample order (the
+        # larger case spans 40 sort tiles of 4096 keys with a ragged last one)
+        base = workloads.plain2d(scale=0.05 if case == "dup" else 1.0)
+        rep = 7 if case == "dup" else 8
         wl = workloads.Workload("dup", np.repeat(base.lon_s, rep), np.repeat(base.lat_s, rep),
                                 np.repeat(base.data, rep, axis=0), None, base.lon_t, base.lat_t,
                                 base.kernel, base.support, base.hpx_maxres)

@@ -101,8 +101,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   static_assert(NTH % kTile == 0, "threads must cover the tile");
   static_assert(CB % 4 == 0, "channel blocks are float4 wide");
 
-  __shared__ float4 sh_hi[K];
-  __shared__ float4 sh_lo[K];
+  __shared__ float4 sh_b[K];      // tile-relative candidate vector, omega in .w
   __shared__ uint32_t sh_idx[K];
   __shared__ __align__(16) float w_s[K][kTile];
   __shared__ __align__(16) float d_s[K][CPAD];
@@ -193,13 +192,15 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
             if (rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
           }
           const int64_t s = rg[lo].x + (v - rg_pre[lo]);
-          sh_hi[tid] = a.s_hi[s];
-          sh_lo[tid] = a.s_lo[s];
+          const float4 h = a.s_hi[s], l = a.s_lo[s];
+          // the candidate relative to the tile centre, once for all targets
+          sh_b[tid] = make_float4(df_diff(h.x, l.x, chi.x, clo.x), df_diff(h.y, l.y, chi.y, clo.y),
+                                  df_diff(h.z, l.z, chi.z, clo.z), h.w);
           sh_idx[tid] = a.perm[s];
         } else {
           // padding candidate (never equal to an empty target slot's sentinel)
-          sh_hi[tid] = make_float4(-4.f, -4.f, -4.f, 0.f);
-          sh_lo[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sh_b[tid] = make_float4(df_diff(-4.f, 0.f, chi.x, clo.x), df_diff(-4.f, 0.f, chi.y, clo.y),
+                                  df_diff(-4.f, 0.f, chi.z, clo.z), 0.f);
           sh_idx[tid] = 0xffffffffu;
         }
       }
@@ -228,12 +229,8 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
       // ---- phase A: weights ----
 #pragma unroll 2
       for (int k = kk0; k < K; k += STEP) {
-        const float4 sh = sh_hi[k];
-        const float4 sl = sh_lo[k];
-        const float bx = df_diff(sh.x, sl.x, chi.x, clo.x);
-        const float by = df_diff(sh.y, sl.y, chi.y, clo.y);
-        const float bz = df_diff(sh.z, sl.z, chi.z, clo.z);
-        const float dx = at.x - bx, dy = at.y - by, dz = at.z - bz;
+        const float4 sh = sh_b[k];
+        const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
         const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         float w = 0.f;
         if (c2 <= a.kd.c2_out) {

@@ -258,7 +258,7 @@ __device__ __forceinline__ uint64_t os_word(uint32_t epoch, uint64_t kind, uint3
 // counts, the look-back finds the tile's offsets, and every key is written
 // to  tile offset + offset of its warp + its rank within the warp  -- the
 // position of the key among equal digits follows its input position (stable).
-__global__ void __launch_bounds__(kThreads) k_os_pass(
+__global__ void __launch_bounds__(kThreads) k_os_pass_warp(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
     const uint32_t* __restrict__ ghist, uint64_t* status, uint32_t* ticket, uint32_t epoch,
@@ -367,6 +367,124 @@ __global__ void __launch_bounds__(kThreads) k_os_pass(
   }
 }
 
+// One pass, ranked block-wide (for inputs of many waves of tiles): the
+// tile's digit counts come from a shared histogram, the look-back publishes
+// the tile's inclusive prefix before the ranking; then the keys are ranked
+// item by item (a round of 256 keys in (item, thread) order per step, warp
+// matches for equal digits, warps in order) and scattered.
+__global__ void __launch_bounds__(kThreads) k_os_pass_block(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+    const uint32_t* __restrict__ ghist, uint64_t* status, uint32_t* ticket, uint32_t epoch,
+    unsigned* err) {
+  __shared__ uint32_t s_b;
+  __shared__ uint32_t blk_off[kRadix];
+  __shared__ uint32_t cnt[kRadix];
+  __shared__ uint32_t wcnt[kWarps][kRadix];
+  __shared__ uint32_t run[kRadix];
+  __shared__ uint32_t warp_sums[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_b = atomicAdd(ticket, 1u);
+  cnt[tid] = 0;
+  run[tid] = 0;
+  __syncthreads();
+  const int64_t b = s_b;
+  const int64_t base = b * kOsTile;
+  // this tile's digit counts
+  uint32_t k_it[kOsItems], v_it[kOsItems];
+#pragma unroll
+  for (int it = 0; it < kOsItems; ++it) {
+    const int64_t i = base + (int64_t)it * kThreads + tid;
+    k_it[it] = 0;
+    v_it[it] = 0;
+    if (i < n) {
+      k_it[it] = kin[i];
+      v_it[it] = vin[i];
+      atomicAdd(&cnt[(k_it[it] >> shift) & 0xffu], 1u);
+    }
+  }
+  __syncthreads();
+  // global exclusive offset of digit tid
+  uint32_t tot;
+  const uint32_t g_excl = block_exclusive_scan(ghist[tid], warp_sums, tot);
+  // publish the count, look back for the prefix, publish the prefix
+  const uint32_t c = cnt[tid];
+  volatile uint64_t* st = status;
+  if (b == 0) {
+    st[(size_t)tid] = os_word(epoch, kInc, c);
+    blk_off[tid] = g_excl;
+  } else {
+    st[(size_t)b * kRadix + tid] = os_word(epoch, kAgg, c);
+    // look back 8 predecessors per step (independent loads), summing in order
+    // until an inclusive prefix; a predecessor not yet published is re-read
+    uint32_t prefix = 0;
+    int64_t j = b - 1;
+    uint32_t spins = 0;
+    const long long t0 = clock64();
+    bool done = false;
+    while (j >= 0 && !done) {
+      uint64_t wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wv[q] = (j - q >= 0) ? st[(size_t)(j - q) * kRadix + tid] : 0;
+      int q = 0;
+      for (; q < 8 && j - q >= 0; ++q) {
+        const uint64_t w = wv[q];
+        const uint64_t kind = (w >> 32) & 3u;
+        if ((uint32_t)(w >> 34) != epoch || kind == 0) break;   // not ready yet
+        prefix += (uint32_t)w;
+        if (kind == kInc) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      j -= q;
+      if (q < 8 && j >= 0) {
+        // never expected to take long: give up after ~1 s and record it
+        if ((++spins & 63u) == 0 && clock64() - t0 > 2000000000LL) {
+          set_error(err, ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    st[(size_t)b * kRadix + tid] = os_word(epoch, kInc, prefix + c);
+    blk_off[tid] = g_excl + prefix;
+  }
+  __syncthreads();
+  // stable ranks in (item, thread) order and scatter
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int it = 0; it < kOsItems; ++it) {
+    const int64_t i = base + (int64_t)it * kThreads + tid;
+    const bool valid = i < n;
+    const unsigned d = valid ? ((k_it[it] >> shift) & 0xffu) : (unsigned)kRadix;
+#pragma unroll
+    for (int w2 = 0; w2 < kWarps; ++w2) wcnt[w2][tid] = 0;
+    __syncthreads();
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t r = run[tid];
+#pragma unroll
+      for (int w2 = 0; w2 < kWarps; ++w2) {
+        const uint32_t cc = wcnt[w2][tid];
+        wcnt[w2][tid] = r;
+        r += cc;
+      }
+      run[tid] = r;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = blk_off[d] + wcnt[wid][d] + rank;
+      kout[pos] = k_it[it];
+      vout[pos] = v_it[it];
+    }
+    __syncthreads();   // wcnt is cleared for the next item
+  }
+}
+
 }  // namespace
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
@@ -401,11 +519,25 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, int key_bi
   k_os_hist<<<hblk, kThreads, 0, s>>>(keys, n, npass, ghist);
   uint32_t *kin = keys, *kout = static_cast<uint32_t*>(w.keys_alt);
   uint32_t *vin = vals, *vout = w.vals_alt;
+  // Warp-ranked passes are faster while the tiles run as one wave (their
+  // look-back waits overlap the ranking); with many waves of tiles the
+  // block-ranked pass keeps more tiles in flight (measured on GB300: 1e6
+  // keys 0.081 vs 0.098 ms, 1e8 keys 8.4 vs 7.6 ms for the sort).
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool warp_ranked = nblk <= 2 * nsm;
   for (int p = 0; p < npass; ++p) {
     w.epoch = (w.epoch + 1) & 0x3fffffffu;
     if (w.epoch == 0) w.epoch = 1;
-    k_os_pass<<<nblk, kThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p, ghist + p * kRadix,
-                                        w.status, tickets + p, w.epoch, w.err);
+    if (warp_ranked)
+      k_os_pass_warp<<<nblk, kThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p,
+                                               ghist + p * kRadix, w.status, tickets + p,
+                                               w.epoch, w.err);
+    else
+      k_os_pass_block<<<nblk, kThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p,
+                                                ghist + p * kRadix, w.status, tickets + p,
+                                                w.epoch, w.err);
     uint32_t* tk = kin; kin = kout; kout = tk;
     uint32_t* tv = vin; vin = vout; vout = tv;
   }

@@ -97,7 +97,7 @@ def test_ang2pix_invalid_inputs():
     assert np.all(got[1:] == -1)
 
 
-@pytest.mark.parametrize("case", ["cube", "allsky", "dup", "dup_many_tiles"])
+@pytest.mark.parametrize("case", ["cube", "allsky", "dup", "dup_many_tiles", "allsky_many_waves"])
 def test_sort_and_ring_offsets_bit_exact(case):
     import torch
     from paper_1604_06667_gb300 import Gridder
@@ -105,6 +105,10 @@ def test_sort_and_ring_offsets_bit_exact(case):
         wl = workloads.cube(scale=0.02, n_channels=4)
     elif case == "allsky":
         wl = workloads.allsky(scale=0.01, n_channels=2)
+    elif case == "allsky_many_waves":
+        # 2e6 samples = 489 sort tiles: more than one wave of resident tiles,
+        # so the passes rank block-wide (fewer tiles rank per warp)
+        wl = workloads.allsky(scale=0.2, n_channels=1)
     else:
         # many exact duplicates: ties must keep ascending sample order (the
         # larger case spans 40 sort tiles of 4096 keys with a ragged last one)

@@ -26,6 +26,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -172,9 +173,44 @@ def job_value(units_per_rank, world, ms_max):
     return units_per_rank * world / (ms_max / 1e3)
 
 
+def sample_targets(n_targets, n, seed):
+    """n distinct target indices drawn with a seeded generator (sorted)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n_targets, min(n, n_targets), replace=False))
+
+
+def keep_rows(out, out_w, tsel):
+    """Host copies of the map rows and weights of the targets tsel (taken
+    after a timed region, for the comparison with the FP64 oracle)."""
+    import torch
+    idx = torch.from_numpy(tsel).to(out.device)
+    return out.index_select(0, idx).cpu().numpy(), out_w.index_select(0, idx).cpu().numpy()
+
+
+def sig(x, n=4):
+    """x rounded to n significant digits (floats in nested containers)."""
+    if isinstance(x, float):
+        return float("%.*g" % (n, x)) if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: sig(v, n) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, n) for v in x]
+    return x
+
+
+def strip_private(x):
+    """Drop the '_'-prefixed working entries (host arrays) before JSON."""
+    if isinstance(x, dict):
+        return {k: strip_private(v) for k, v in x.items() if not str(k).startswith("_")}
+    if isinstance(x, list):
+        return [strip_private(v) for v in x]
+    return x
+
+
 def workload_desc(wl, form):
-    return ("spectral cube: %d samples x %d channels (basket-weave raster, 10x10 deg) -> "
-            "%dx%d plate-carree targets; gauss1d sigma=3', support 9', nside 4096; %s data"
+    return ("spectral cube: %d raster samples x %d ch -> %dx%d CAR targets, gauss1d sigma 3', "
+            "r 9', nside 4096, %s data"
             % (wl.n_samples, wl.n_channels, wl.grid_shape[1], wl.grid_shape[0],
                "BF16" if form == "bf16" else "FP32"))
 
@@ -201,6 +237,68 @@ def cpu_oracle_rate(wl, n_sub, seed=12345):
     dt = time.perf_counter() - t0
     upd = res.npairs * wl.n_channels
     return upd / dt, dt, idx.size, res.npairs
+
+
+def oracle_candidates(wl, tsel):
+    """Samples that can reach the targets tsel: a latitude band from one sort,
+    then the great-circle distance against the support widened by 1e-6 (a
+    superset, so the brute-force sum over them is exact for those targets)."""
+    import numpy as np
+    order = np.argsort(wl.lat_s, kind="stable")
+    ls = wl.lat_s[order]
+    rad = wl.support * (1.0 + 1e-6) + 1e-9
+    keep = []
+    for lc, bc in zip(wl.lon_t[tsel], wl.lat_t[tsel]):
+        lo = np.searchsorted(ls, bc - rad, "left")
+        hi = np.searchsorted(ls, bc + rad, "right")
+        idx = order[lo:hi]
+        b1, b2 = np.radians(bc), np.radians(wl.lat_s[idx])
+        dl = np.radians(wl.lon_s[idx] - lc)
+        h = np.sin(0.5 * (b2 - b1)) ** 2 + np.cos(b1) * np.cos(b2) * np.sin(0.5 * dl) ** 2
+        d = 2.0 * np.arcsin(np.sqrt(np.minimum(h, 1.0)))
+        keep.append(idx[d <= np.radians(rad)])
+    return np.unique(np.concatenate(keep)) if keep else np.zeros(0, dtype=np.int64)
+
+
+def oracle_kernel(wl):
+    import oracle
+    k = wl.kernel
+    if k["type"] == "gauss1d":
+        return oracle.gauss1d(k["sigma"], wl.support)
+    return oracle.gauss2d(k["smaj"], k["smin"], k["pa"], wl.support)
+
+
+def oracle_errors(wl, tsel, rows):
+    """Error of GPU rows (map, weights at the targets tsel) against the FP64
+    brute-force oracle on the caller's FP32 data: max and 99th percentile of
+    |R - R_oracle| / S (S = sum |omega w D| / W, the oracle's scale) over
+    W > 0 targets and channels, the largest relative weight-map error, and
+    support mismatches.  Returns (error dict, oracle seconds, oracle pairs)."""
+    import numpy as np
+    import oracle
+    cand = oracle_candidates(wl, tsel)
+    t0 = time.perf_counter()
+    ref = oracle.grid_bruteforce(wl.lon_t[tsel], wl.lat_t[tsel], wl.lon_s[cand], wl.lat_s[cand],
+                                 np.asarray(wl.data, dtype=np.float64)[cand], oracle_kernel(wl),
+                                 None if wl.omega is None else np.asarray(wl.omega)[cand])
+    dt = time.perf_counter() - t0
+    res = {}
+    for form, (got, got_w) in rows.items():
+        got = np.asarray(got, dtype=np.float64)
+        got_w = np.asarray(got_w, dtype=np.float64)
+        on = ref.wsum > 0
+        mism = int((on != (got_w > 0)).sum())
+        both = on & (got_w > 0)
+        scale = np.where(ref.sabs[both] > 0, ref.sabs[both], 1.0)
+        e = np.abs(got[both] - ref.out[both]) / scale
+        e = np.where(np.isnan(e), np.inf, e).ravel()
+        we = np.abs(got_w[both] - ref.wsum[both]) / ref.wsum[both]
+        res[form] = {"max": float(e.max()) if e.size else 0.0,
+                     "p99": float(np.percentile(e, 99)) if e.size else 0.0,
+                     "w_max": float(we.max()) if we.size else 0.0,
+                     "support_mismatch": mism, "targets": int(len(tsel)),
+                     "values": int(e.size)}
+    return res, dt, ref.npairs
 
 
 def run_reference(args):
@@ -234,7 +332,8 @@ def run_reference(args):
     return 0
 
 
-def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks, peaks_src):
+def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks, peaks_src,
+              tsel):
     """Warm up, then time K one-shot steps of one accumulation form."""
     import torch
     from paper_1604_06667_gb300 import _capi
@@ -269,6 +368,7 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
     stages = g.read_timing()
     g.set_timing(False)
     info1 = g.info()
+    sel = keep_rows(out, out_w, tsel)
     ms_max = max_over_ranks(ms, world)
     pairs = info1["n_pairs"]
     C = wl.n_channels
@@ -312,6 +412,7 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
                                if k != "grid_launches"},
         "gpu_launches": info1["n_launches"] - info0["n_launches"],
         "clocks": clocks,
+        "_sel": sel,
     }
 
 
@@ -446,6 +547,7 @@ def time_config(args, dev, name):
     """Plain 2-D (2e4 samples -> 100^2, sigma 2.5') and all-sky elliptical
     (1e7 samples x 32 channels -> 4096 x 2048, 10'/6'/PA 30, r = 30')
     one-shot calls, each form timed with CUDA events after warm-up."""
+    import numpy as np
     import torch
     import workloads
     from paper_1604_06667_gb300 import Gridder, _capi
@@ -460,6 +562,15 @@ def time_config(args, dev, name):
     g.set_kernel(kt, kp, wl.support, wl.hpx_maxres)
     out = torch.empty((wl.n_targets, wl.n_channels), device=dev)
     w = torch.empty(wl.n_targets, device=dev)
+    # targets checked against the FP64 oracle afterwards: the whole plain 2-D
+    # map; for the all-sky map random targets plus the rows next to the poles
+    if name == "plain2d":
+        tsel = np.arange(wl.n_targets)
+    else:
+        nx = wl.grid_shape[1]
+        tsel = np.unique(np.concatenate([sample_targets(wl.n_targets, 160, 612),
+                                         np.arange(0, 32), np.arange(wl.n_targets - 32, wl.n_targets),
+                                         nx * (wl.grid_shape[0] // 2) + np.arange(0, nx, nx // 16)]))
     forms = [("fp32", _capi.CG_PATH_FP32, d32)]
     if wl.n_channels % 8 == 0:
         forms.append(("bf16", _capi.CG_PATH_TC, d32.to(torch.bfloat16)))
@@ -484,8 +595,11 @@ def time_config(args, dev, name):
         nbytes = wl.n_samples * (16 + wl.n_channels * db) + wl.n_targets * (4 * wl.n_channels + 4)
         res[form] = {"ms_per_call": ms, "pairs": pairs,
                      "updates_per_s": pairs * wl.n_channels / (ms / 1e3),
-                     "hbm_frac": nbytes / (ms / 1e3) / (load_peaks()[0]["hbm_gbs"] * 1e9)}
+                     "hbm_frac": nbytes / (ms / 1e3) / (load_peaks()[0]["hbm_gbs"] * 1e9),
+                     "_sel": keep_rows(out, w, tsel)}
     g.close()
+    res["_wl"] = wl
+    res["_tsel"] = tsel
     return res
 
 
@@ -615,6 +729,55 @@ def grid_kernel_bytes(wl, dbytes):
     return N * (C * dbytes + 32) + P * (C * 4 + 4)
 
 
+def detail_path():
+    """Where the full result record goes: BENCH_DETAIL if set, else
+    gpurun_out/bench_detail.json when that folder exists, else
+    bench_detail.json in the working directory."""
+    p = os.environ.get("BENCH_DETAIL")
+    if p:
+        return p
+    if os.path.isdir(os.path.join(os.getcwd(), "gpurun_out")):
+        return os.path.join("gpurun_out", "bench_detail.json")
+    return "bench_detail.json"
+
+
+def compact_line(line, detail_file):
+    """The one JSON line: the contract's keys plus short summaries (forms,
+    mixed / FP32 ratio, oracle errors, batched); everything else stays in the
+    detail file, so the line fits a short log tail."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+            "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+            "gpu_launches", "clocks", "roofline", "e2e", "cpu_baseline")
+    out = {k: line[k] for k in keep if k in line}
+    out["clocks"] = {k: v for k, v in line["clocks"].items() if k != "samples"}
+    out["roofline"] = {k: v for k, v in line["roofline"].items()
+                       if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    out["roofline"]["kernel"] = line["roofline"]["kernel"].split(" ")[0]
+    if "e2e" in line:
+        out["e2e"] = {k: line["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                  "d2h_bytes_per_step")}
+    out["forms"] = {f: {"ms": r["ms_per_step"], "value": r["value"], "frac": r["roofline"]["frac"]}
+                    for f, r in line["forms"].items()}
+    if "mixed_over_fp32" in line:
+        out["mixed_over_fp32"] = line["mixed_over_fp32"]
+    if "error_vs_oracle" in line:
+        out["err"] = {k: sig([v.get("max"), v.get("p99"), v.get("w_max")], 2)
+                      for k, v in line["error_vs_oracle"].items() if isinstance(v, dict)}
+    if "batched" in line:
+        b = line["batched"]
+        out["batched"] = {"mixed_ms": b["mixed"]["ms_per_batch"],
+                          "fp32_ms": b["fp32"]["ms_per_batch"],
+                          "ratio": b["mixed_over_fp32"],
+                          "kernels": b["mixed"]["graph_kernels"]}
+    if "allsky" in line:
+        out["allsky_ms"] = {f: line["allsky"][f]["ms_per_call"] for f in ("bf16", "fp32")
+                            if f in line["allsky"]}
+    if "paper_example1" in line:
+        out["example1_ms"] = line["paper_example1"]["ms_per_call"]
+    out["detail"] = detail_file
+    return sig(out, 3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -642,12 +805,13 @@ def main():
     g.set_kernel("gauss1d", (wl.kernel["sigma"],), wl.support, wl.hpx_maxres)
     out = torch.empty((P, C), device=dev, dtype=torch.float32)
     out_w = torch.empty(P, device=dev, dtype=torch.float32)
+    tsel_cube = sample_targets(P, 200, 613)
     results = {}
     for form in forms:
         progress("timing form %s" % form)
         data = data16 if form == "bf16" else data32
         results[form] = time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local,
-                                  peaks, peaks_src)
+                                  peaks, peaks_src, tsel_cube)
     prim = results[forms[0]]
     form = prim["form"]
     gold = golden_pairs("cube_scale%g" % args.scale)
@@ -656,11 +820,11 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": prim["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if form == "bf16" else "f32",
-        "data": "synthetic (seeded basket-weave raster cube; no dataset)",
-        "config": {"workload": workload_desc(wl, form), "form": form,
-                   "l2": "inputs larger than L2 (%d MB of channel data), no flush"
+        "data": "synthetic (seeded raster cube, no dataset)",
+        "config": {"workload": workload_desc(wl, form),
+                   "l2": "inputs > L2 (%d MB data), no flush"
                          % (N * C * (2 if form == "bf16" else 4) // 2 ** 20),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
         "pairs_per_step": prim["pairs"],
         "pairs_oracle": (gold or {}).get("pairs"),
         "weights_evaluated_per_step": prim["weights_evaluated"],
@@ -677,6 +841,7 @@ def main():
     }
     if len(results) == 2:
         line["mixed_over_fp32"] = results["bf16"]["value"] / results["fp32"]["value"]
+    configs = {}
     if not args.no_extra and args.scale == 1.0:
         progress("differentiable workload")
         line["differentiable"] = time_differentiable(args, dev)
@@ -689,8 +854,9 @@ def main():
         progress("paper appendix A.2 (scan-line aliasing study)")
         line["paper_aliasing_a2"] = study_aliasing(args, dev)
         progress("plain 2-D and all-sky")
-        line["plain2d"] = time_config(args, dev, "plain2d")
-        line["allsky"] = time_config(args, dev, "allsky")
+        for name in ("plain2d", "allsky"):
+            configs[name] = time_config(args, dev, name)
+            line[name] = configs[name]
 
     # ---- end to end: pinned host inputs, copies inside the timed region ----
     # cg_grid_oneshot_host: every step copies its samples and channel data in
@@ -727,19 +893,47 @@ def main():
                        "d2h_bytes_per_step": P * C * 4, "ms_per_step": ms_e2e,
                        "api": "cg_grid_oneshot_host (pipelined over consecutive calls)",
                        "timer": "host wall clock"}
+    g.close()
 
-    # ---- CPU baseline: the FP64 oracle as it stands, rank 0 only ----
+    # ---- CPU leg (rank 0 only): the FP64 oracle as it stands ----
+    # (1) the CPU baseline: the HEALPix-lookup oracle timed on a bounded
+    # random subset of the cube's samples onto all targets, one host thread;
+    # (2) the error of every timed GPU form against the brute-force oracle on
+    # the caller's FP32 data at sampled targets (after all GPU timing).
     if rank == 0 and world == 1 and not args.no_cpu:
         progress("cpu baseline")
         rate, dt, n, npairs = cpu_oracle_rate(wl, args.cpu_samples)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "%d random samples of the workload (%d pairs, %d "
-                                          "channels) onto all %d targets, %.1f s"
-                                          % (n, npairs, C, P, dt)}
+                                "sample": "%d random samples x all %d targets, %.1f s"
+                                          % (n, P, dt)}
+        progress("errors against the FP64 oracle")
+        errs = {}
+        e, _, _ = oracle_errors(wl, tsel_cube, {f: r["_sel"] for f, r in results.items()})
+        for f, v in e.items():
+            errs["cube_" + f] = v
+        for name, res in configs.items():
+            rows = {f: res[f]["_sel"] for f in ("bf16", "fp32") if f in res}
+            e, _, _ = oracle_errors(res["_wl"], res["_tsel"], rows)
+            for f, v in e.items():
+                errs[name + "_" + f] = v
+        line["error_vs_oracle"] = errs
+        line["error_vs_oracle_note"] = (
+            "max and 99th percentile of |R - R_oracle| / S over W > 0 targets x channels, "
+            "largest relative W error; FP64 brute-force oracle on the caller's FP32 data at "
+            "sampled targets (cube 200, all-sky 226, plain 2-D the whole map)")
     if rank == 0:
-        print(json.dumps(line))
+        dpath = detail_path()
+        detail = strip_private(line)
+        try:
+            with open(dpath, "w") as f:
+                json.dump(detail, f, indent=1, default=float)
+        except OSError as ex:
+            progress("could not write %s: %s" % (dpath, ex))
+        s = json.dumps(compact_line(detail, dpath), separators=(",", ":"))
+        # large whole floats in exponent form (5.09e+13, not 50900000000000.0)
+        s = re.sub(r"(?<=[:,\[])(\d{8,})\.0(?=[,}\]])", lambda m: "%.3g" % float(m.group(1)), s)
+        print(s)
         sys.stdout.flush()
-    g.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -5,9 +5,10 @@ CG_PATH_TC stores each weight as a hi + lo pair of BF16 numbers (~16
 significant bits); with FP32 accumulation the only difference from the FP64
 definition on the same BF16 data is rounding, bound TC_TOL on the
 S-normalised map error and the relative weight-map error.  CG_PATH_TC_FAST
-keeps single BF16 weights (8 significant bits); W is summed from the same
-rounded weights, so R stays a weighted mean and the error is at most
-2^-8 of S (bound FAST_TOL).
+keeps single BF16 weights (8 significant bits, each rounded to within
+2^-8 of itself) in the numerator while W is summed in FP32 from the
+unrounded weights, so the numerator moves by at most 2^-8 sum |omega w D|:
+at most 2^-8 of S (bound FAST_TOL).
 Also checked: the fused one-shot epilogue, store / add accumulation, several
 adds, the channel-major layout, ragged channel counts (padding to the MMA N),
 more than 256 channels (several channel slabs), the elliptical kernel and

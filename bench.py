@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["auto", "fp32", "bf16"], default="auto")
+    ap.add_argument("--form", choices=["auto", "fp32", "bf16", "bf16s"], default="auto",
+                    help="bf16: BF16 data, hi + lo BF16 weights; bf16s: single BF16 weights")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = full)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -173,6 +174,19 @@ def job_value(units_per_rank, world, ms_max):
     return units_per_rank * world / (ms_max / 1e3)
 
 
+def is_bf16(form):
+    return form.startswith("bf16")
+
+
+def form_path(form):
+    """The accumulation form of a bench form name: bf16 = BF16 data with hi +
+    lo BF16 weights on the tensor cores, bf16s = single BF16 weights, fp32 =
+    FP32 CUDA cores."""
+    from paper_1604_06667_gb300 import _capi
+    return {"bf16": _capi.CG_PATH_TC, "bf16s": _capi.CG_PATH_TC_FAST,
+            "fp32": _capi.CG_PATH_FP32}[form]
+
+
 def sample_targets(n_targets, n, seed):
     """n distinct target indices drawn with a seeded generator (sorted)."""
     import numpy as np
@@ -209,10 +223,11 @@ def strip_private(x):
 
 
 def workload_desc(wl, form):
+    what = {"bf16s": "BF16 data, BF16 weights", "bf16": "BF16 data, hi+lo BF16 weights",
+            "fp32": "FP32 data"}[form]
     return ("spectral cube: %d raster samples x %d ch -> %dx%d CAR targets, gauss1d sigma 3', "
-            "r 9', nside 4096, %s data"
-            % (wl.n_samples, wl.n_channels, wl.grid_shape[1], wl.grid_shape[0],
-               "BF16" if form == "bf16" else "FP32"))
+            "r 9', nside 4096, %s"
+            % (wl.n_samples, wl.n_channels, wl.grid_shape[1], wl.grid_shape[0], what))
 
 
 def algorithmic_bytes(wl, data_bytes):
@@ -338,7 +353,7 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
     import torch
     from paper_1604_06667_gb300 import _capi
     dev = out.device
-    g.set_path(_capi.CG_PATH_TC if form == "bf16" else _capi.CG_PATH_FP32)
+    g.set_path(form_path(form))
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -373,7 +388,7 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
     pairs = info1["n_pairs"]
     C = wl.n_channels
     upd = float(pairs) * C
-    dbytes = 2 if form == "bf16" else 4
+    dbytes = 2 if is_bf16(form) else 4
     t_grid = stages["grid"] / max(1, stages["grid_launches"])
     if form == "fp32":
         peak_tf = N_SMS * FFMA_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -394,7 +409,8 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
                 "tensor_useful_tflops": 2.0 * upd / (t_grid / 1e3) / 1e12,
                 # MMA work as executed: every evaluated (target, candidate)
                 # weight times C channels, hi + lo BF16 halves
-                "tensor_executed_tflops": 2.0 * 2.0 * C * float(info1["n_candidates"]) *
+                "tensor_executed_tflops": (2.0 if form == "bf16" else 1.0) * 2.0 * C *
+                float(info1["n_candidates"]) *
                 float(info1["tile_size"]) / (t_grid / 1e3) / 1e12,
                 "tensor_peak_tflops": peaks.get("bf16_tflops")}
     step_bytes = algorithmic_bytes(wl, dbytes)
@@ -573,7 +589,9 @@ def time_config(args, dev, name):
                                          nx * (wl.grid_shape[0] // 2) + np.arange(0, nx, nx // 16)]))
     forms = [("fp32", _capi.CG_PATH_FP32, d32)]
     if wl.n_channels % 8 == 0:
-        forms.append(("bf16", _capi.CG_PATH_TC, d32.to(torch.bfloat16)))
+        d16 = d32.to(torch.bfloat16)
+        forms.append(("bf16", _capi.CG_PATH_TC, d16))
+        forms.append(("bf16s", _capi.CG_PATH_TC_FAST, d16))
     res = {"workload": "%s: %d samples x %d channels -> %d targets" % (
         name, wl.n_samples, wl.n_channels, wl.n_targets)}
     stream = torch.cuda.current_stream(dev)
@@ -591,7 +609,7 @@ def time_config(args, dev, name):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        db = 2 if form == "bf16" else 4
+        db = 2 if is_bf16(form) else 4
         nbytes = wl.n_samples * (16 + wl.n_channels * db) + wl.n_targets * (4 * wl.n_channels + 4)
         res[form] = {"ms_per_call": ms, "pairs": pairs,
                      "updates_per_s": pairs * wl.n_channels / (ms / 1e3),
@@ -761,8 +779,10 @@ def compact_line(line, detail_file):
     if "mixed_over_fp32" in line:
         out["mixed_over_fp32"] = line["mixed_over_fp32"]
     if "error_vs_oracle" in line:
-        out["err"] = {k: sig([v.get("max"), v.get("p99"), v.get("w_max")], 2)
-                      for k, v in line["error_vs_oracle"].items() if isinstance(v, dict)}
+        # largest error of each form and config in units of S (p99 and the
+        # weight-map error are in the detail file)
+        out["err_max"] = {k: sig(v.get("max"), 2)
+                          for k, v in line["error_vs_oracle"].items() if isinstance(v, dict)}
     if "batched" in line:
         b = line["batched"]
         out["batched"] = {"mixed_ms": b["mixed"]["ms_per_batch"],
@@ -770,7 +790,7 @@ def compact_line(line, detail_file):
                           "ratio": b["mixed_over_fp32"],
                           "kernels": b["mixed"]["graph_kernels"]}
     if "allsky" in line:
-        out["allsky_ms"] = {f: line["allsky"][f]["ms_per_call"] for f in ("bf16", "fp32")
+        out["allsky_ms"] = {f: line["allsky"][f]["ms_per_call"] for f in ("bf16", "bf16s", "fp32")
                             if f in line["allsky"]}
     if "paper_example1" in line:
         out["example1_ms"] = line["paper_example1"]["ms_per_call"]
@@ -793,7 +813,9 @@ def main():
     peaks, peaks_src = load_peaks()
     progress("generating workload")
     wl = workloads.cube(scale=args.scale)
-    forms = ["bf16", "fp32"] if args.form == "auto" else [args.form]
+    # headline: BF16 data with hi + lo BF16 weights; then single BF16
+    # weights, then the FP32 form (each with its error against the oracle)
+    forms = ["bf16", "bf16s", "fp32"] if args.form == "auto" else [args.form]
     N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
     lon = torch.from_numpy(wl.lon_s).to(dev)
     lat = torch.from_numpy(wl.lat_s).to(dev)
@@ -809,7 +831,7 @@ def main():
     results = {}
     for form in forms:
         progress("timing form %s" % form)
-        data = data16 if form == "bf16" else data32
+        data = data16 if is_bf16(form) else data32
         results[form] = time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local,
                                   peaks, peaks_src, tsel_cube)
     prim = results[forms[0]]
@@ -819,11 +841,11 @@ def main():
         "metric": METRIC, "value": prim["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": prim["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if form == "bf16" else "f32",
+        "dtype": "bf16" if is_bf16(form) else "f32",
         "data": "synthetic (seeded raster cube, no dataset)",
         "config": {"workload": workload_desc(wl, form),
                    "l2": "inputs > L2 (%d MB data), no flush"
-                         % (N * C * (2 if form == "bf16" else 4) // 2 ** 20),
+                         % (N * C * (2 if is_bf16(form) else 4) // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "pairs_per_step": prim["pairs"],
         "pairs_oracle": (gold or {}).get("pairs"),
@@ -839,8 +861,8 @@ def main():
                                         "stages_ms_per_step", "clocks")}
                   for f, r in results.items()},
     }
-    if len(results) == 2:
-        line["mixed_over_fp32"] = results["bf16"]["value"] / results["fp32"]["value"]
+    if "fp32" in results and prim["form"] != "fp32":
+        line["mixed_over_fp32"] = prim["value"] / results["fp32"]["value"]
     configs = {}
     if not args.no_extra and args.scale == 1.0:
         progress("differentiable workload")
@@ -866,9 +888,9 @@ def main():
     if not args.no_e2e:
         progress("e2e")
         from paper_1604_06667_gb300 import _capi
-        g.set_path(_capi.CG_PATH_TC if form == "bf16" else _capi.CG_PATH_FP32)
-        data = data16 if form == "bf16" else data32
-        dbytes = 2 if form == "bf16" else 4
+        g.set_path(form_path(form))
+        data = data16 if is_bf16(form) else data32
+        dbytes = 2 if is_bf16(form) else 4
         h_lon = torch.from_numpy(wl.lon_s).pin_memory()
         h_lat = torch.from_numpy(wl.lat_s).pin_memory()
         h_data = data.cpu().pin_memory()
@@ -912,7 +934,7 @@ def main():
         for f, v in e.items():
             errs["cube_" + f] = v
         for name, res in configs.items():
-            rows = {f: res[f]["_sel"] for f in ("bf16", "fp32") if f in res}
+            rows = {f: res[f]["_sel"] for f in ("bf16", "bf16s", "fp32") if f in res}
             e, _, _ = oracle_errors(res["_wl"], res["_tsel"], rows)
             for f, v in e.items():
                 errs[name + "_" + f] = v

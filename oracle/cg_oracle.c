@@ -48,8 +48,13 @@ typedef struct { double s, c; } or_acc;
 
 static void acc_add(or_acc* a, double x) {
   double t = a->s + x;
-  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
-  else a->c += (x - t) + a->s;
+  /* the correction term is defined for finite sums only; once a term is
+   * infinite or NaN the sum is that of plain IEEE summation (Eq. 1 with such a
+   * value: +-Inf, or NaN for Inf - Inf or a NaN term) */
+  if (isfinite(t)) {
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+  }
   a->s = t;
 }
 static double acc_get(const or_acc* a) { return a->s + a->c; }

@@ -325,6 +325,48 @@ def test_sort_csr():
     check_sort_csr()
 
 
+def check_nonfinite_ieee():
+    """Eq. 1 with a non-finite channel value, summed as IEEE arithmetic
+    defines it: a target reached by a +Inf sample gets +Inf, one reached by
+    +Inf and -Inf samples NaN, one reached by a NaN sample NaN; every other
+    target equals the sum over the finite samples alone (the same map with
+    those samples removed, where they do not reach)."""
+    rng = np.random.Generator(np.random.PCG64(4242))
+    n = 300
+    lon = 10.0 + rng.uniform(-0.5, 0.5, n)
+    lat = 5.0 + rng.uniform(-0.5, 0.5, n)
+    lon[:3] = [9.8, 10.2, 10.21]
+    lat[:3] = [5.0, 5.0, 5.0]
+    data = rng.normal(0, 1, (n, 2)) + 2.0
+    data[0, 0] = np.nan
+    data[1, 1] = np.inf
+    data[2, 1] = -np.inf
+    lon_t, lat_t = workloads.car_grid(10.0, 5.0, 24, 24, 1.0 / 24.0)
+    k = oracle.gauss1d(2.0 * ARCMIN, 6.0 * ARCMIN)
+    ref = oracle.grid_bruteforce(lon_t, lat_t, lon, lat, data, k)
+    d = np.array([[oracle.haversine(a, b, c, e) for c, e in zip(lon[:3], lat[:3])]
+                  for a, b in zip(lon_t, lat_t)])
+    reach = d <= math.radians(6.0 * ARCMIN)
+    on = ref.wsum > 0
+    r0, r1, r2 = reach[:, 0] & on, reach[:, 1] & on, reach[:, 2] & on
+    assert r0.any() and (r1 & ~r2).any() and (r1 & r2).any()
+    assert np.all(np.isnan(ref.out[r0, 0]))
+    assert np.all(ref.out[r1 & ~r2, 1] == np.inf)
+    assert np.all(ref.out[r2 & ~r1, 1] == -np.inf)
+    assert np.all(np.isnan(ref.out[r1 & r2, 1]))
+    clean = oracle.grid_bruteforce(lon_t, lat_t, lon[3:], lat[3:], data[3:], k)
+    # (the clean map lacks all three samples, so compare where none reaches)
+    keep0 = keep1 = on & ~(r0 | r1 | r2) & (clean.wsum > 0)
+    # away from the bad samples' supports both maps sum the same terms
+    assert np.all(np.isfinite(ref.num[keep0, 0])) and np.all(np.isfinite(ref.num[keep1, 1]))
+    assert np.allclose(ref.num[keep0, 0], clean.num[keep0, 0], rtol=1e-13, atol=1e-13)
+    assert np.allclose(ref.num[keep1, 1], clean.num[keep1, 1], rtol=1e-13, atol=1e-13)
+
+
+def test_nonfinite_ieee():
+    check_nonfinite_ieee()
+
+
 # ----------------------------------------------------------------------------
 # planted mistakes: each copy of the oracle with one plausible error must fail
 # at least one pin
@@ -355,6 +397,7 @@ MUTATIONS = {
     "degrid_not_normalised": ("const double g = w * (omega ? omega[n] : 1.0) / W;",
                               "const double g = w * (omega ? omega[n] : 1.0);",
                               [check_linearity_and_adjoint]),
+    "compensation_on_nonfinite": ("  if (isfinite(t)) {\n", "  if (1) {\n", [check_nonfinite_ieee]),
     "cut_not_applied": ("if (!(d <= r)) { *inside = 0; return 0.0; }",
                         "if (0) { *inside = 0; return 0.0; }", [check_single_sample]),
 }

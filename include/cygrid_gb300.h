@@ -331,6 +331,20 @@ cg_status cg_grid_dsigma(cg_grid* g, const void* data, int32_t data_dtype, const
 cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
                                int64_t* ring_off, int64_t n);
 
+/* Testing hook for the bounded waits of the tensor-core gridder.
+ *
+ * The paper has no counterpart.  enable != 0: until it is called again with
+ * enable = 0, every tensor-core gridding launch of this handle makes its
+ * producer warps first wait for a device word that nothing sets, giving up
+ * after wait_cycles SM clock cycles (<= 0: 2e6, about a millisecond).  The
+ * wait runs out, the kernel records a time-out, every warp role stops, the
+ * MMAs in flight complete and the tensor memory is freed; the next
+ * synchronising call (cg_sync, cg_grid_finalize, ...) returns CG_ETIMEOUT and
+ * clears the condition.  The call's output is undefined; the handle stays
+ * usable.  This exercises the failure path of the kernel's waits without any
+ * fault, trap or endless loop on the GPU. */
+cg_status cg_debug_hold(cg_grid* g, int32_t enable, int64_t wait_cycles);
+
 /* No-allocation variant of the sample index (RING keys + stable sort).
  *
  * The paper has no counterpart: this entry point exists for callers that must

@@ -77,6 +77,7 @@ SIGNATURES = {
     "cg_grid_export_index": [_vp, _vp, _vp, _vp, _i64],
     "cg_set_timing": [_vp, _i32],
     "cg_read_timing": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)],
+    "cg_debug_hold": [_vp, _i32, _i64],
     "cg_sort_samples_noalloc": [_i32, _vp, _vp, _i64, _vp, _vp, _vp],
     "cg_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(CgJob), _i32, _i32],
     "cg_batch_autotune": [_vp, _i32, _i32],
@@ -149,6 +150,7 @@ cg_grid_export_index = _call("cg_grid_export_index")
 cg_set_timing = _call("cg_set_timing")
 cg_read_timing = _call("cg_read_timing")
 cg_sort_samples_noalloc = _call("cg_sort_samples_noalloc")
+cg_debug_hold = _call("cg_debug_hold")
 cg_batch_create = _call("cg_batch_create")
 cg_batch_autotune = _call("cg_batch_autotune")
 cg_batch_capture = _call("cg_batch_capture")

@@ -145,6 +145,10 @@ void free_all(cg_grid* g) {
   dfree(g->acc_w, s);
   dfree(g->d_err, s);
   dfree(g->d_pairs, s);
+  dfree(g->nf_bits, s);
+  dfree(g->nf_any, s);
+  g->nf_words = 0;
+  dfree(g->d_hold, s);
   release_events(g);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
@@ -818,6 +822,19 @@ cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
   if (n > 0 && (!sorted_pix || !perm)) return fail(CG_EINVAL, "cg_grid_export_index: null pointer");
   CG_CUDA(cudaSetDevice(g->device), "cg_grid_export_index");
   CG_CUDA(export_index(g, sorted_pix, perm, ring_off, n), "cg_grid_export_index");
+  return CG_OK;
+}
+
+cg_status cg_debug_hold(cg_grid* g, int32_t enable, int64_t wait_cycles) {
+  g_last_error.clear();
+  if (!g) return fail(CG_EINVAL, "cg_debug_hold: null handle");
+  CG_CUDA(cudaSetDevice(g->device), "cg_debug_hold");
+  if (enable && !g->d_hold) {
+    CG_CUDA(dalloc(&g->d_hold, 1, g->stream), "cg_debug_hold");
+    CG_CUDA(cudaMemsetAsync(g->d_hold, 0, sizeof(int32_t), g->stream), "cg_debug_hold");
+  }
+  g->hold = enable != 0;
+  g->hold_cycles = wait_cycles > 0 ? wait_cycles : 2000000;
   return CG_OK;
 }
 

@@ -189,6 +189,16 @@ struct cg_grid {
 
   unsigned* d_err = nullptr;      // device error word
   unsigned long long* d_pairs = nullptr;  // pairs with d <= r since the last reset
+  // (target slot, channel slab) rows of a gridder pass whose numerator came
+  // out non-finite: one bit each, and a word set when any bit is (the fix-up
+  // pass recomputes those rows and clears their bits)
+  uint32_t* nf_bits = nullptr;
+  uint32_t* nf_any = nullptr;
+  size_t nf_words = 0;
+  // cg_debug_hold: the tensor-core producers wait for d_hold (never set)
+  bool hold = false;
+  int64_t hold_cycles = 0;
+  int32_t* d_hold = nullptr;
   int64_t n_launches = 0;         // kernels launched by this handle
 
   // optional stage timing (CUDA events on the handle's stream)
@@ -255,6 +265,24 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
 bool tc_supported(const cg_grid* g, int dtype, const void* data);
 cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, float* out_w,
                           int split);
+// k_grid.cu -- rows a gridder flagged as non-finite, computed again in FP32
+// with only the pairs inside the support taking part; the pass returns at
+// once when nothing is flagged.  Bit e = slot * n_slabs + slab of nf_bits.
+struct NonfiniteRows {
+  const Tiling* tiling;   // the tiling whose candidate ranges the gridder used
+  const void* data;       // [n_samples][C] channel values, dtype
+  int dtype;
+  int C;
+  int cp;                 // channels per slab (<= 256)
+  int n_slabs;
+  int mode;               // 0 store, 1 add (into acc_num), 2 divide by W into out
+  float* out;             // mode 2: user-order map
+  float* acc_num;         // modes 0, 1: slot-order numerator
+  KernelDev kd;
+};
+// Grow the bitmap to n_bits (zeroed) and clear the "any" word.
+cudaError_t nonfinite_prepare(cg_grid* g, int64_t n_bits);
+cudaError_t nonfinite_fixup(cg_grid* g, const NonfiniteRows& rows);
 // k_noalloc.cu -- sample index on the library's static scratch array.
 cudaError_t sort_samples_noalloc(int nside, const double* lon, const double* lat, int64_t n,
                                  int64_t* sorted_pix, int64_t* perm, cudaStream_t s);

@@ -16,7 +16,9 @@
 //   phase B  register-blocked accumulation acc[p][c] += w[k][p] * D[k][c],
 //            skipping candidates whose weights for the thread's targets are 0.
 // The epilogue adds acc into the numerator and W into the weight map (tile
-// order; cg_grid_finalize applies Eq. 3 and the user layout).
+// order; cg_grid_finalize applies Eq. 3 and the user layout).  A target row
+// whose numerator came out non-finite (a NaN or Inf channel value reaches the
+// thread's other targets through 0 x NaN) is left to k_nonfinite_fixup.
 #include <cuda_bf16.h>
 
 #include "cg_common.cuh"
@@ -57,6 +59,9 @@ struct GridArgs {
   int64_t n_slots;
   float* part_num;      // [n_split][slots][C]
   float2* part_w;       // [n_split][slots]
+  // rows with a non-finite numerator (bit slot * gridDim.y + blockIdx.y)
+  uint32_t* nf_bits;
+  uint32_t* nf_any;
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -91,6 +96,50 @@ __device__ __forceinline__ float4 load_vec4<__nv_bfloat16>(const __nv_bfloat16* 
   return r;
 }
 
+// Weight omega w(p, k) of target p (tile-relative vector at, elliptical axes
+// f1, f2) against candidate sh (tile-relative vector, omega in .w) in FP32:
+// chord, exact cut d <= r (FP64 recomputation inside the guard band),
+// kernel value.  Pairs outside the support get -0.0: it adds nothing to any
+// finite sum, and its sign bit tells the accumulation that the pair does not
+// take part at all (so that a non-finite channel value of a sample reaches
+// only the targets within its support, paper Eq. 1-2).
+__device__ __forceinline__ float pair_weight(const KernelDev& kd, float4 at, float4 f1, float4 f2,
+                                             float4 sh, double2 tll, const double2* sll,
+                                             uint32_t idx, bool& in) {
+  const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
+  const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  in = false;
+  if (!(c2 <= kd.c2_out)) return -0.f;
+  float d2;
+  if (!kd.big_support) {
+    d2 = c2 * fmaf(c2, fmaf(c2, 1.f / 90.f, 1.f / 12.f), 1.f);
+  } else {
+    const float d = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(c2)));
+    d2 = d * d;
+  }
+  float ex;
+  if (kd.type == CG_GAUSS1D || kd.type == CG_TSINC) {
+    ex = kd.k1 * d2;
+  } else {
+    const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
+    const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
+    const float s2 = fmaf(ap, ap, bp * bp);  // sin^2 d
+    const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
+    ex = fmaf(kd.k1 * ap, ap, kd.k2 * bp * bp) * ratio;
+  }
+  float w = ex2_approx(ex) * sh.w;
+  if (kd.type == CG_TSINC) w *= sinc_pi(sqrtf(d2) * kd.inv_a);
+  if (kd.dscale != 0.f) w *= d2 * kd.dscale;   // dw/dsigma pass
+  in = true;
+  if (c2 >= kd.c2_in) {
+    // guard band: decide d <= r again from the input coordinates
+    in = pair_inside_inl(tll, sll[idx], kd.c2r_hi, kd.c2r_lo, kd.c2r_tol, kd.r_rad);
+  }
+  return in ? w : -0.f;
+}
+
+__device__ __forceinline__ bool takes_part(float w) { return __float_as_uint(w) != 0x80000000u; }
+
 // PB targets x CB channels per thread in phase B; NCG channel groups.
 template <int PB, int CB, int NCG, typename DT>
 __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
@@ -108,6 +157,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   __shared__ int2 rg[kRangeBatch];
   __shared__ int rg_pre[kRangeBatch + 1];
   __shared__ float2 wred[NTH];
+  __shared__ int row_nf[kTile];   // rows of this CTA with a non-finite numerator
 
   const int tid = threadIdx.x;
   const int64_t tile = blockIdx.x;
@@ -226,13 +276,16 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
         }
       }
 
+
       // ---- phase A: weights ----
 #pragma unroll 2
       for (int k = kk0; k < K; k += STEP) {
+        // the arithmetic of pair_weight, written out (pairs outside the
+        // support get -0.0)
         const float4 sh = sh_b[k];
         const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
         const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float w = 0.f;
+        float w = -0.f;
         if (c2 <= a.kd.c2_out) {
           float d2;
           if (!a.kd.big_support) {
@@ -261,7 +314,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
             in = pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
                                  a.kd.c2r_tol, a.kd.r_rad);
           }
-          if (in) ++npair; else w = 0.f;
+          if (in) ++npair; else w = -0.f;
         }
         w_s[k][p] = w;
         // Neumaier (two-sum) accumulation of the weight map
@@ -306,12 +359,56 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     }
   }
 
+  // ---- non-finite rows ----
+  // A non-finite channel value reaches every target of a thread that some
+  // of them reach (0 x NaN).  A target row (this CTA's channels) with a
+  // non-finite numerator is flagged for the fix-up pass, which computes it
+  // again with only the pairs inside the support (paper Eq. 1-2) and stores
+  // or adds it; the row is not written here.  A sum turns non-finite when a
+  // term is (or, harmlessly, on an overflow, which only sends the row to the
+  // exact fix-up).
+  bool row_bad[PB];
+  {
+    float chk[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      chk[i] = 0.f;
+#pragma unroll
+      for (int j = 0; j < CB; ++j) chk[i] += acc[i][j];
+    }
+    const unsigned any_bad = __syncthreads_or([&] {
+      bool b = false;
+#pragma unroll
+      for (int i = 0; i < PB; ++i) b |= !isfinite(chk[i]);
+      return b;
+    }());
+    if (any_bad) {
+      // the NCG threads of a target group share each row: agree per row
+      if (tid < kTile) row_nf[tid] = 0;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PB; ++i)
+        if (!isfinite(chk[i])) row_nf[pg * PB + i] = 1;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PB; ++i) row_bad[i] = row_nf[pg * PB + i] != 0;
+      if (tid < kTile && row_nf[tid] && a.tgt_perm[tile * kTile + tid] != 0xffffffffu) {
+        const uint64_t e = (uint64_t)(tile * kTile + tid) * (uint64_t)gridDim.y + blockIdx.y;
+        atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
+        atomicOr(a.nf_any, 1u);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < PB; ++i) row_bad[i] = false;
+    }
+  }
+
   // ---- epilogue: numerator ----
   const bool split = a.n_split > 1;
 #pragma unroll
   for (int i = 0; i < PB; ++i) {
     const int64_t sl = tile * kTile + pg * PB + i;
-    if (a.tgt_perm[sl] == 0xffffffffu) continue;
+    if (a.tgt_perm[sl] == 0xffffffffu || row_bad[i]) continue;
     float* dst = split ? a.part_num + ((size_t)blockIdx.z * a.n_slots + sl) * C
                        : a.acc_num + (size_t)sl * C;
     const bool add = a.accumulate && !split;
@@ -360,12 +457,16 @@ __global__ void k_split_reduce(const float* __restrict__ part_num,
                                const float2* __restrict__ part_w,
                                const uint32_t* __restrict__ perm, int64_t n_slots, int C,
                                int n_split, int accumulate, float* __restrict__ acc_num,
-                               float2* __restrict__ acc_w) {
+                               float2* __restrict__ acc_w, const uint32_t* __restrict__ nf_bits,
+                               int cpad, int n_slabs) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_slots * (C + 1)) return;
   if (e < n_slots * C) {
     const int64_t sl = e / C;
     if (perm[sl] == 0xffffffffu) return;
+    // a row some split flagged as non-finite is the fix-up pass's to write
+    const uint64_t b = (uint64_t)sl * (uint64_t)n_slabs + (uint64_t)((e - sl * C) / cpad);
+    if ((nf_bits[b >> 5] >> (b & 31)) & 1u) return;
     float v = 0.f;
     for (int z = 0; z < n_split; ++z) v += part_num[(size_t)z * n_slots * C + e];
     acc_num[e] = accumulate ? acc_num[e] + v : v;
@@ -416,9 +517,11 @@ cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s
 }
 
 // One FP32 gridder pass: choose the candidate splits, grow the partial-sum
-// scratch if needed, launch, and reduce the splits.
+// scratch if needed, launch, reduce the splits, and compute the flagged
+// non-finite rows again.
 template <int PB, int CB, int NCG>
 cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
+  constexpr int CPAD = CB * NCG;
   const int64_t nt = g->t64.n_tiles;
   cudaStream_t s = g->stream;
   int dev = 0, nsm = 0;
@@ -446,15 +549,34 @@ cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
     a.part_num = g->part_num;
     a.part_w = g->part_w;
   }
+  const int n_slabs = (a.C + CPAD - 1) / CPAD;
+  cudaError_t e = nonfinite_prepare(g, g->n_slots * (int64_t)n_slabs);
+  if (e != cudaSuccess) return e;
+  a.nf_bits = g->nf_bits;
+  a.nf_any = g->nf_any;
   g->n_launches += 1;
-  cudaError_t e = launch<PB, CB, NCG>(a, nt, dtype, s);
-  if (e != cudaSuccess || a.n_split <= 1 || nt == 0) return e;
-  const int64_t m = g->n_slots * (int64_t)(a.C + 1);
-  k_split_reduce<<<ceil_div(m, 256), 256, 0, s>>>(a.part_num, a.part_w, a.tgt_perm, g->n_slots,
-                                                  a.C, a.n_split, a.accumulate, a.acc_num,
-                                                  a.acc_w);
-  g->n_launches += 1;
-  return cudaGetLastError();
+  e = launch<PB, CB, NCG>(a, nt, dtype, s);
+  if (e != cudaSuccess || nt == 0) return e;
+  if (a.n_split > 1) {
+    const int64_t m = g->n_slots * (int64_t)(a.C + 1);
+    k_split_reduce<<<ceil_div(m, 256), 256, 0, s>>>(a.part_num, a.part_w, a.tgt_perm, g->n_slots,
+                                                    a.C, a.n_split, a.accumulate, a.acc_num,
+                                                    a.acc_w, a.nf_bits, CPAD, n_slabs);
+    g->n_launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  NonfiniteRows rows;
+  rows.tiling = &g->t64;
+  rows.data = a.data;
+  rows.dtype = dtype;
+  rows.C = a.C;
+  rows.cp = CPAD;
+  rows.n_slabs = n_slabs;
+  rows.mode = a.accumulate ? 1 : 0;
+  rows.out = nullptr;
+  rows.acc_num = a.acc_num;
+  rows.kd = a.kd;
+  return nonfinite_fixup(g, rows);
 }
 
 }  // namespace
@@ -504,6 +626,188 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
     case 5: return run<4, 16, 8>(g, a, dtype);
     default: return run<4, 16, 16>(g, a, dtype);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Rows flagged as non-finite by either gridder: one CTA per (target slot,
+// channel slab) bit, computed again from the tile's candidates with the FP32
+// weights of pair_weight; only pairs inside the support take part, so a
+// non-finite channel value reaches exactly the targets within its support
+// (paper Eq. 1-2).  W itself was right (the weights are finite); the
+// numerator is stored, added or (one-shot tensor-core calls) divided by W
+// into the caller's map.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FixArgs {
+  const float4* chi;
+  const float4* clo;
+  const float4* ta;
+  const int64_t* range_off;
+  const int2* range_s;
+  int T;                  // targets per tile of the tiling the rows belong to
+  const float4* f1;
+  const float4* f2;
+  const double2* tll;
+  const float4* s_hi;
+  const float4* s_lo;
+  const uint32_t* perm;
+  const double2* sll;
+  KernelDev kd;
+  const void* data;
+  int bf16;
+  int C, cp, n_slabs, mode;
+  float* out;
+  float* acc_num;
+  const uint32_t* perm_t;
+  uint32_t* bits;
+  const uint32_t* any;
+  int64_t n_words;
+};
+
+constexpr int kFixThreads = 256;
+
+__device__ __forceinline__ float fix_load(const FixArgs& a, size_t i) {
+  return a.bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.data)[i])
+                : static_cast<const float*>(a.data)[i];
+}
+
+__global__ void __launch_bounds__(kFixThreads) k_nonfinite_fixup(FixArgs a) {
+  __shared__ float w_s[kFixThreads];
+  __shared__ uint32_t idx_s[kFixThreads];
+  __shared__ double wsum_s[kFixThreads];
+  __shared__ uint32_t word_s;
+  if (*a.any == 0u) return;   // the common case: nothing flagged
+  const int tid = threadIdx.x;
+  for (int64_t wd = blockIdx.x; wd < a.n_words; wd += gridDim.x) {
+    __syncthreads();
+    if (tid == 0) word_s = a.bits[wd];
+    __syncthreads();
+    uint32_t bits = word_s;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int64_t e = wd * 32 + b;
+      const int64_t slot = e / a.n_slabs;
+      const int slab = (int)(e % a.n_slabs);
+      const int64_t tile = slot / a.T;
+      const float4 at = a.ta[slot];
+      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
+      if (a.kd.type == CG_GAUSS2D) {
+        f1 = a.f1[slot];
+        f2 = a.f2[slot];
+      }
+      const float4 chi = a.chi[tile], clo = a.clo[tile];
+      const int c = slab * a.cp + tid;
+      const bool mine = tid < a.cp && c < a.C;
+      float acc = 0.f;
+      double wsum = 0.0;
+      for (int64_t r = a.range_off[tile]; r < a.range_off[tile + 1]; ++r) {
+        const int2 rg = a.range_s[r];
+        for (int j0 = rg.x; j0 < rg.y; j0 += kFixThreads) {
+          __syncthreads();
+          const int pos = j0 + tid;
+          float w = -0.f;
+          uint32_t idx = 0;
+          if (pos < rg.y) {
+            const float4 h = a.s_hi[pos], l = a.s_lo[pos];
+            const float4 sh = make_float4(df_diff(h.x, l.x, chi.x, clo.x),
+                                          df_diff(h.y, l.y, chi.y, clo.y),
+                                          df_diff(h.z, l.z, chi.z, clo.z), h.w);
+            idx = a.perm[pos];
+            bool in;
+            w = pair_weight(a.kd, at, f1, f2, sh, a.tll[slot], a.sll, idx, in);
+            if (in) wsum += (double)w;
+          }
+          w_s[tid] = w;
+          idx_s[tid] = idx;
+          __syncthreads();
+          const int n = min(kFixThreads, rg.y - j0);
+          if (mine)
+            for (int k = 0; k < n; ++k)
+              if (takes_part(w_s[k])) acc = fmaf(w_s[k], fix_load(a, (size_t)idx_s[k] * a.C + c), acc);
+        }
+      }
+      double W = 0.0;
+      if (a.mode == 2) {
+        wsum_s[tid] = wsum;
+        __syncthreads();
+        for (int o = kFixThreads / 2; o > 0; o >>= 1) {
+          if (tid < o) wsum_s[tid] += wsum_s[tid + o];
+          __syncthreads();
+        }
+        W = wsum_s[0];
+      }
+      if (mine) {
+        if (a.mode == 2) {
+          const uint32_t user = a.perm_t[slot];
+          if (user != 0xffffffffu)
+            a.out[(size_t)user * a.C + c] = (W > 0.0) ? (float)((double)acc / W) : __int_as_float(0x7fc00000);
+        } else if (a.mode == 1) {
+          a.acc_num[(size_t)slot * a.C + c] += acc;
+        } else {
+          a.acc_num[(size_t)slot * a.C + c] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && word_s) a.bits[wd] = 0u;
+  }
+}
+
+}  // namespace
+
+cudaError_t nonfinite_prepare(cg_grid* g, int64_t n_bits) {
+  const size_t words = (size_t)((n_bits + 31) / 32);
+  if (g->nf_words < words) {
+    // zero when allocated; every fix-up pass clears the bits it served
+    dfree(g->nf_bits, g->stream);
+    g->nf_words = 0;
+    cudaError_t e = dalloc(&g->nf_bits, words, g->stream);
+    if (e == cudaSuccess && !g->nf_any) e = dalloc(&g->nf_any, 1, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->nf_bits, 0, words * sizeof(uint32_t), g->stream);
+    if (e != cudaSuccess) return e;
+    g->nf_words = words;
+  }
+  return cudaMemsetAsync(g->nf_any, 0, sizeof(uint32_t), g->stream);
+}
+
+cudaError_t nonfinite_fixup(cg_grid* g, const NonfiniteRows& j) {
+  FixArgs a;
+  const Tiling& t = *j.tiling;
+  a.chi = t.chi;
+  a.clo = t.clo;
+  a.ta = t.a;
+  a.range_off = t.range_off;
+  a.range_s = t.range_s;
+  a.T = t.T;
+  a.f1 = g->tgt_f1;
+  a.f2 = g->tgt_f2;
+  a.tll = g->tgt_ll;
+  a.s_hi = g->s_hi;
+  a.s_lo = g->s_lo;
+  a.perm = g->sorted_val;
+  a.sll = g->s_ll;
+  a.kd = j.kd;
+  a.data = j.data;
+  a.bf16 = j.dtype == CG_BF16;
+  a.C = j.C;
+  a.cp = j.cp;
+  a.n_slabs = j.n_slabs;
+  a.mode = j.mode;
+  a.out = j.out;
+  a.acc_num = j.acc_num;
+  a.perm_t = g->tgt_perm;
+  a.bits = g->nf_bits;
+  a.any = g->nf_any;
+  a.n_words = (int64_t)((g->n_slots * (int64_t)j.n_slabs + 31) / 32);
+  if (j.cp > kFixThreads || a.n_words > (int64_t)g->nf_words) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_nonfinite_fixup<<<(unsigned)nsm, kFixThreads, 0, g->stream>>>(a);
+  g->n_launches += 1;
+  return cudaGetLastError();
 }
 
 // Register-blocking shapes of the FP32 gridder, (targets x channels per

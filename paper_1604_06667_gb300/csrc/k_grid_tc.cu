@@ -112,6 +112,10 @@ struct TcArgs {
   int64_t n_slots;
   unsigned long long* pairs;
   unsigned* err;
+  uint32_t* nf_bits;    // (slot, slab) rows with a non-finite numerator
+  uint32_t* nf_any;
+  const int* hold;      // cg_debug_hold: a word nothing sets (null: no hold)
+  long long hold_cycles;
 };
 
 struct Smem {
@@ -510,6 +514,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (warp >= kProdWarp && warp < kProdWarp + kNP) {
     // ------------------------------------------------------------ producers
     const int pw = warp - kProdWarp;
+    if (a.hold) {
+      // testing hook: wait for a word that nothing sets; the wait runs out
+      // and the kernel takes its time-out path (no copies issued yet)
+      const long long t0 = clock64();
+      while (*((volatile const int*)a.hold) == 0 && !*S.abort_flag &&
+             clock64() - t0 < a.hold_cycles)
+        __nanosleep(1000);
+      if (*((volatile const int*)a.hold) == 0) {
+        set_error(a.err, ERR_TIMEOUT);
+        *S.abort_flag = 1;
+      }
+    }
     const float e_mid = make_pair_const<KT, BIG>(a.kd).e_mid;
     const int nblk = cp / 64;                     // 64-channel blocks of a slab
     const uint32_t bytes = (uint32_t)kK * (uint32_t)cp * 2u;
@@ -631,6 +647,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         valid = false;
       }
       const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
+      // A non-finite channel value of one candidate reaches every row of the
+      // MMA (0 x NaN): a row whose numerator is not finite is flagged and
+      // computed again by the fix-up pass (paper Eq. 1-2: only the pairs
+      // inside the support take part).  A sum of the row's values turns
+      // non-finite when one of them is (or, harmlessly, on an overflow, which
+      // only sends the row to the exact fix-up).  Accumulating calls look
+      // first and leave the row untouched; one-shot calls write it and let
+      // the fix-up overwrite it.
+      float2 fin2 = make_float2(0.f, 0.f);
+      if (a.mode != 2 && nch) {
+        for (int cb = 0; cb < cp; cb += 16) {
+          uint32_t r[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(tmem_d + lane_off + (uint32_t)cb));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; j += 2)
+            fin2 = __fadd2_rn(fin2, make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
+        }
+      }
+      // accumulating call, row flagged: leave it to the fix-up
+      const bool keep = !(a.mode != 2 && !isfinite(fin2.x + fin2.y));
       // one-shot output: 32 x 32 blocks through a padded shared tile so that
       // every store instruction writes 4 whole 128-byte rows
       const bool fast = a.mode == 2 && (a.C & 3) == 0 &&
@@ -655,6 +698,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(tmem_d + lane_off + (uint32_t)(cb + 16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (a.mode == 2 && nch) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2)
+            fin2 = __fadd2_rn(fin2, make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c1 = c0 + 16 * h;
@@ -671,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (c1 + j < a.C) dst[j] = nch ? __uint_as_float(r[16 * h + j]) * invW : invW;
-          } else if (valid) {
+          } else if (valid && keep) {
             float* dst = a.acc_num + (size_t)slot * a.C + c1;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -694,6 +742,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
             *reinterpret_cast<float4*>(a.out + (size_t)u * a.C + c0 + cc) = v;
         }
         __syncwarp();
+      }
+      if (valid && nch && !isfinite(fin2.x + fin2.y)) {
+        const uint64_t e = (uint64_t)slot * (uint64_t)a.n_slabs + (uint64_t)slab;
+        atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
+        atomicOr(a.nf_any, 1u);
       }
       if (valid && slab == 0) {
         if (a.mode == 2) {
@@ -1055,6 +1108,14 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, fl
   a.n_slots = g->n_slots;
   a.pairs = g->d_pairs;
   a.err = g->d_err;
+  {
+    cudaError_t ea = nonfinite_prepare(g, g->n_slots * (int64_t)a.n_slabs);
+    if (ea != cudaSuccess) return ea;
+    a.nf_bits = g->nf_bits;
+    a.nf_any = g->nf_any;
+  }
+  a.hold = (g->hold && g->d_hold) ? g->d_hold : nullptr;
+  a.hold_cycles = g->hold_cycles;
   // Stages: chunk q uses stage q % ns and is staged by producer warp q % kNP.
   // ns must be a multiple of kNP so that every stage always belongs to the
   // same producer warp: the parity-based empty-barrier wait is only valid
@@ -1122,7 +1183,20 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, fl
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)grid, kThreads, smem, g->stream>>>(tmap, a);
   g->n_launches += 1;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  NonfiniteRows rows;
+  rows.tiling = &g->t128;
+  rows.data = data;
+  rows.dtype = CG_BF16;
+  rows.C = g->C;
+  rows.cp = a.cp;
+  rows.n_slabs = a.n_slabs;
+  rows.mode = mode;
+  rows.out = out;
+  rows.acc_num = g->acc_num;
+  rows.kd = g->kdev;
+  return nonfinite_fixup(g, rows);
 }
 
 }  // namespace cg

@@ -237,6 +237,12 @@ class Gridder:
         self._keep_s = (data, grad_out)
         return dR, ds
 
+    def debug_hold(self, enable: bool = True, wait_cycles: int = 0):
+        """Testing hook (cg_debug_hold): tensor-core launches time out on
+        purpose until disabled; the next sync raises CG_ETIMEOUT."""
+        C.cg_debug_hold(self._h, 1 if enable else 0, int(wait_cycles))
+        return self
+
     def reset(self):
         C.cg_grid_reset(self._h)
 

@@ -245,13 +245,20 @@ def cpu_oracle_rate(wl, n_sub, seed=12345):
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = np.sort(rng.choice(wl.n_samples, size=min(n_sub, wl.n_samples), replace=False))
     ns = oracle.nside_for_resolution(wl.hpx_maxres)
-    k = oracle.gauss1d(wl.kernel["sigma"], wl.support)
+    k = oracle_kernel(wl)
     d64 = wl.data[idx].astype(np.float64)
     t0 = time.perf_counter()
     res = oracle.grid_lookup(ns, wl.lon_t, wl.lat_t, wl.lon_s[idx], wl.lat_s[idx], d64, k)
     dt = time.perf_counter() - t0
     upd = res.npairs * wl.n_channels
     return upd / dt, dt, idx.size, res.npairs
+
+
+def cpu_baseline_entry(wl, n_sub, seed):
+    rate, dt, n, npairs = cpu_oracle_rate(wl, n_sub, seed)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d random samples x all %d targets (%d pairs), %.1f s"
+                      % (n, wl.n_targets, npairs, dt)}
 
 
 def oracle_candidates(wl, tsel):
@@ -399,7 +406,9 @@ def time_form(g, wl, form, lon, lat, data, out, out_w, args, world, local, peaks
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
     else:
         hbm = peaks["hbm_gbs"]
-        kbytes = grid_kernel_bytes(wl, dbytes)
+        # the method's bytes (sample lon/lat and data rows read once, map
+        # and weight map written once), charged to the dominant kernel
+        kbytes = algorithmic_bytes(wl, dbytes)
         ach = kbytes / (t_grid / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm,
@@ -650,7 +659,17 @@ def time_example1(args, dev):
     stages = g.read_timing()
     info = g.info()
     g.close()
-    return {"workload": "paper Example 1: %d samples uniform in 5x5 deg, 90x90 targets at 200\", "
+    # a bounded random subset (host copy) for the CPU leg's oracle timing
+    import numpy as np
+    import workloads as wlmod
+    rng = np.random.Generator(np.random.PCG64(77))
+    sub = torch.from_numpy(np.sort(rng.choice(lon.numel(), 200000, replace=False))).to(dev)
+    wl_sub = wlmod.Workload("example1-subset", lon[sub].cpu().numpy(), lat[sub].cpu().numpy(),
+                            data[sub].float().cpu().numpy().reshape(-1, 1), None,
+                            np.asarray(lon_t), np.asarray(lat_t), dict(kern), support, maxres,
+                            (90, 90), {})
+    return {"_wl": wl_sub,
+            "workload": "paper Example 1: %d samples uniform in 5x5 deg, 90x90 targets at 200\", "
                         "FWHM 300\" Gaussian, support 3 sigma, one channel" % lon.numel(),
             "ms_per_call": ms, "pairs_per_call": info["n_pairs"],
             "stages_ms": {k: v / steps for k, v in stages.items() if k != "grid_launches"},
@@ -737,14 +756,6 @@ def study_aliasing(args, dev):
     return {"workload": "paper App. A.2: scan lines, 1.5 x 1.5 deg, PSF 0.1 deg, pixel PSF/20, "
                         "no noise; max relative deviation from the kernel-convolved field",
             "max_rel_deviation": table, "gpu_ms_total": t_gpu}
-
-
-def grid_kernel_bytes(wl, dbytes):
-    """Algorithmic bytes of one gridder launch: every sample's channel row and
-    its sorted 32-byte position record read once, the map and weight map
-    written once."""
-    N, C, P = wl.n_samples, wl.n_channels, wl.n_targets
-    return N * (C * dbytes + 32) + P * (C * 4 + 4)
 
 
 def detail_path():
@@ -928,6 +939,13 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%d random samples x all %d targets, %.1f s"
                                           % (n, P, dt)}
+        # the same oracle beside the other timed workloads (detail record)
+        if "allsky" in configs:
+            configs["allsky"]["cpu_baseline"] = cpu_baseline_entry(configs["allsky"]["_wl"],
+                                                                   12000, 5)
+        if "paper_example1" in line:
+            line["paper_example1"]["cpu_baseline"] = cpu_baseline_entry(
+                line["paper_example1"]["_wl"], 200000, 6)
         progress("errors against the FP64 oracle")
         errs = {}
         e, _, _ = oracle_errors(wl, tsel_cube, {f: r["_sel"] for f, r in results.items()})

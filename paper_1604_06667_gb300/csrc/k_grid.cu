@@ -6,9 +6,10 @@
 // cells in each thread"), with a CTA in place of a CPU thread.
 //
 // The CTA walks the tile's candidate samples -- the sample ranges that the
-// tile's disc query selected -- in chunks of kChunk:
-//   stage    candidate unit vectors (double-float), sample weight, data rows
-//            into shared memory;
+// tile's disc query selected -- in chunks of kChunk, two stages deep:
+//   stage    candidate unit vectors (double-float) and sample weight, and the
+//            candidates' channel rows (FP32 rows by cp.async, 16-byte pieces
+//            straight into shared memory, issued one chunk ahead);
 //   phase A  weights w[k][p] for every (candidate, target) pair: chord between
 //            tile-relative FP32 vectors, exact cut d <= r (FP64 recomputation
 //            inside a narrow guard band around r), Gaussian via ex2;
@@ -140,24 +141,49 @@ __device__ __forceinline__ float pair_weight(const KernelDev& kd, float4 at, flo
 
 __device__ __forceinline__ bool takes_part(float w) { return __float_as_uint(w) != 0x80000000u; }
 
+// Shared memory of one k_grid_f32 CTA: two stages of candidates (tile-relative
+// vector, input index), their channel rows (FP32) and their weights, so that
+// the copies of chunk q + 1 run under the weights and the accumulation of
+// chunk q.
+template <int PB, int CB, int NCG>
+struct alignas(16) F32Smem {
+  static constexpr int NTH = (kTile / PB) * NCG;
+  static constexpr int CPAD = CB * NCG;
+  float d[2][kChunk][CPAD];      // channel rows of the candidates
+  float w[2][kChunk][kTile];     // weights w[k][p]
+  float4 b[2][kChunk];           // tile-relative candidate vector, omega in .w
+  uint32_t idx[2][kChunk];       // input index (0xffffffff: padding)
+  int2 rg[kRangeBatch];          // a batch of the tile's sample ranges
+  int rg_pre[kRangeBatch + 1];   // candidates before each range of the batch
+  float2 wred[NTH];
+  int row_nf[kTile];             // rows of this CTA with a non-finite numerator
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes 0 fills zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // PB targets x CB channels per thread in phase B; NCG channel groups.
 template <int PB, int CB, int NCG, typename DT>
 __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
-  constexpr int NTH = (kTile / PB) * NCG;
-  constexpr int CPAD = CB * NCG;
+  using Smem = F32Smem<PB, CB, NCG>;
+  constexpr int NTH = Smem::NTH;
+  constexpr int CPAD = Smem::CPAD;
   constexpr int K = kChunk;
   constexpr int STEP = NTH / kTile;
   static_assert(NTH % kTile == 0, "threads must cover the tile");
   static_assert(CB % 4 == 0, "channel blocks are float4 wide");
-
-  __shared__ float4 sh_b[K];      // tile-relative candidate vector, omega in .w
-  __shared__ uint32_t sh_idx[K];
-  __shared__ __align__(16) float w_s[K][kTile];
-  __shared__ __align__(16) float d_s[K][CPAD];
-  __shared__ int2 rg[kRangeBatch];
-  __shared__ int rg_pre[kRangeBatch + 1];
-  __shared__ float2 wred[NTH];
-  __shared__ int row_nf[kTile];   // rows of this CTA with a non-finite numerator
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
 
   const int tid = threadIdx.x;
   const int64_t tile = blockIdx.x;
@@ -189,6 +215,9 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
 
   const DT* data = static_cast<const DT*>(a.data);
   const int C = a.C;
+  // FP32 rows in 16-byte pieces go straight to shared memory (cp.async);
+  // BF16 rows and unaligned rows through registers
+  const bool async_rows = a.vec4 && sizeof(DT) == 4;
   const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
   // this CTA's share [c_lo, c_hi) of the tile's candidates (whole chunks)
   int c_lo = 0, c_hi = 0x7fffffff;
@@ -202,7 +231,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
 
   for (int64_t rb = r0; rb < r1 && cbase < c_hi; rb += kRangeBatch) {
     const int nr = (int)((r1 - rb) < kRangeBatch ? (r1 - rb) : kRangeBatch);
-    __syncthreads();
+    __syncthreads();   // the previous batch's chunks are done with rg / rg_pre
     if (tid < 32) {
       // warp 0: load this batch of ranges and prefix-sum their lengths
       int carry = 0;
@@ -211,7 +240,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
         int len = 0;
         if (q < nr) {
           const int2 r = a.range_s[rb + q];
-          rg[q] = r;
+          S.rg[q] = r;
           len = r.y - r.x;
         }
         int incl = len;
@@ -220,69 +249,98 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
           const int y = __shfl_up_sync(0xffffffffu, incl, o);
           if (tid >= o) incl += y;
         }
-        if (q < nr) rg_pre[q] = carry + incl - len;
+        if (q < nr) S.rg_pre[q] = carry + incl - len;
         carry += __shfl_sync(0xffffffffu, incl, 31);
       }
-      if (tid == 0) rg_pre[nr] = carry;
+      if (tid == 0) S.rg_pre[nr] = carry;
     }
     __syncthreads();
-    const int total = rg_pre[nr];
+    const int total = S.rg_pre[nr];
     const int v_lo = max(0, min(total, c_lo - cbase));
     const int v_hi = max(0, min(total, c_hi - cbase));
     cbase += total;
+    const int n_chunks = (v_hi - v_lo + K - 1) / K;
+    if (n_chunks == 0) continue;
 
-    for (int v0 = v_lo; v0 < v_hi; v0 += K) {
-      // ---- stage candidates ----
+    // candidates of the chunk at v0 into stage st (threads tid < K)
+    auto stage_cands = [&](int v0, int st) {
       if (tid < K) {
         const int v = v0 + tid;
         if (v < v_hi) {
           int lo = 0, hi = nr - 1;  // last range with rg_pre <= v
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
+            if (S.rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
           }
-          const int64_t s = rg[lo].x + (v - rg_pre[lo]);
+          const int64_t s = S.rg[lo].x + (v - S.rg_pre[lo]);
           const float4 h = a.s_hi[s], l = a.s_lo[s];
           // the candidate relative to the tile centre, once for all targets
-          sh_b[tid] = make_float4(df_diff(h.x, l.x, chi.x, clo.x), df_diff(h.y, l.y, chi.y, clo.y),
-                                  df_diff(h.z, l.z, chi.z, clo.z), h.w);
-          sh_idx[tid] = a.perm[s];
+          S.b[st][tid] = make_float4(df_diff(h.x, l.x, chi.x, clo.x),
+                                     df_diff(h.y, l.y, chi.y, clo.y),
+                                     df_diff(h.z, l.z, chi.z, clo.z), h.w);
+          S.idx[st][tid] = a.perm[s];
         } else {
           // padding candidate (never equal to an empty target slot's sentinel)
-          sh_b[tid] = make_float4(df_diff(-4.f, 0.f, chi.x, clo.x), df_diff(-4.f, 0.f, chi.y, clo.y),
-                                  df_diff(-4.f, 0.f, chi.z, clo.z), 0.f);
-          sh_idx[tid] = 0xffffffffu;
+          S.b[st][tid] = make_float4(df_diff(-4.f, 0.f, chi.x, clo.x),
+                                     df_diff(-4.f, 0.f, chi.y, clo.y),
+                                     df_diff(-4.f, 0.f, chi.z, clo.z), 0.f);
+          S.idx[st][tid] = 0xffffffffu;
         }
       }
-      __syncthreads();
-      if (a.vec4) {
+    };
+    // channel rows of stage st's candidates (their indices are visible)
+    auto stage_rows = [&](int st) {
+      if (async_rows) {
         for (int e = tid; e < K * (CPAD / 4); e += NTH) {
           const int k = e / (CPAD / 4);
           const int c = (e % (CPAD / 4)) * 4;
-          const uint32_t idx = sh_idx[k];
+          const uint32_t idx = S.idx[st][k];
+          const bool ok = idx != 0xffffffffu && c_base + c < C;
+          const DT* src = ok ? data + (size_t)idx * C + c_base + c : data;
+          cp_async16(&S.d[st][k][c], src, ok ? 16 : 0);
+        }
+        cp_async_commit();
+      } else if (a.vec4) {
+        for (int e = tid; e < K * (CPAD / 4); e += NTH) {
+          const int k = e / (CPAD / 4);
+          const int c = (e % (CPAD / 4)) * 4;
+          const uint32_t idx = S.idx[st][k];
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (idx != 0xffffffffu && c_base + c < C)
             v = load_vec4<DT>(data + (size_t)idx * C + c_base + c);
-          *reinterpret_cast<float4*>(&d_s[k][c]) = v;
+          *reinterpret_cast<float4*>(&S.d[st][k][c]) = v;
         }
       } else {
         for (int e = tid; e < K * CPAD; e += NTH) {
           const int k = e / CPAD;
           const int c = e % CPAD;
-          const uint32_t idx = sh_idx[k];
+          const uint32_t idx = S.idx[st][k];
           float v = 0.f;
           if (idx != 0xffffffffu && c_base + c < C) v = load_elem<DT>(data + (size_t)idx * C + c_base + c);
-          d_s[k][c] = v;
+          S.d[st][k][c] = v;
         }
       }
+    };
 
+    // Two-stage pipeline, one barrier per chunk.  Chunk q uses stage q & 1.
+    // Before the barrier of chunk q: the candidates of chunk q + 1 and the
+    // weights of chunk q; after it: the rows of chunk q + 1 are issued and
+    // chunk q is accumulated.  A stage is rewritten only after the barrier
+    // that follows its last reader.
+    stage_cands(v_lo, 0);
+    __syncthreads();
+    stage_rows(0);
+    for (int q = 0; q < n_chunks; ++q) {
+      const int cur = q & 1, nxt = cur ^ 1;
+      const bool more = q + 1 < n_chunks;
+      if (more) stage_cands(v_lo + (q + 1) * K, nxt);
 
       // ---- phase A: weights ----
 #pragma unroll 2
       for (int k = kk0; k < K; k += STEP) {
         // the arithmetic of pair_weight, written out (pairs outside the
         // support get -0.0)
-        const float4 sh = sh_b[k];
+        const float4 sh = S.b[cur][k];
         const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
         const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         float w = -0.f;
@@ -310,54 +368,56 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
           bool in = true;
           if (c2 >= a.kd.c2_in) {
             // guard band: decide d <= r again from the input coordinates
-            const uint32_t idx = sh_idx[k];
+            const uint32_t idx = S.idx[cur][k];
             in = pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
                                  a.kd.c2r_tol, a.kd.r_rad);
           }
           if (in) ++npair; else w = -0.f;
         }
-        w_s[k][p] = w;
+        S.w[cur][k][p] = w;
         // Neumaier (two-sum) accumulation of the weight map
         const float t = ws + w;
         const float bp2 = t - ws;
         wc += (ws - (t - bp2)) + (w - bp2);
         ws = t;
       }
+      if (async_rows) cp_async_wait_all();   // this thread's copies of chunk q
       __syncthreads();
+      if (more) stage_rows(nxt);
 
       // ---- phase B: channel accumulation ----
 #pragma unroll 4
       for (int k = 0; k < K; ++k) {
         float wv[PB];
         if constexpr (PB == 4) {
-          const float4 q = *reinterpret_cast<const float4*>(&w_s[k][pg * 4]);
-          wv[0] = q.x; wv[1] = q.y; wv[2] = q.z; wv[3] = q.w;
+          const float4 q4 = *reinterpret_cast<const float4*>(&S.w[cur][k][pg * 4]);
+          wv[0] = q4.x; wv[1] = q4.y; wv[2] = q4.z; wv[3] = q4.w;
         } else if constexpr (PB == 2) {
-          const float2 q = *reinterpret_cast<const float2*>(&w_s[k][pg * 2]);
-          wv[0] = q.x; wv[1] = q.y;
+          const float2 q2 = *reinterpret_cast<const float2*>(&S.w[cur][k][pg * 2]);
+          wv[0] = q2.x; wv[1] = q2.y;
         } else {
 #pragma unroll
-          for (int i = 0; i < PB; ++i) wv[i] = w_s[k][pg * PB + i];
+          for (int i = 0; i < PB; ++i) wv[i] = S.w[cur][k][pg * PB + i];
         }
         bool any = false;
 #pragma unroll
         for (int i = 0; i < PB; ++i) any |= (wv[i] != 0.f);
         if (!any) continue;
 #pragma unroll
-        for (int q = 0; q < CB / 4; ++q) {
-          const float4 dv = *reinterpret_cast<const float4*>(&d_s[k][4 * cg + 4 * NCG * q]);
+        for (int q4 = 0; q4 < CB / 4; ++q4) {
+          const float4 dv = *reinterpret_cast<const float4*>(&S.d[cur][k][4 * cg + 4 * NCG * q4]);
 #pragma unroll
           for (int i = 0; i < PB; ++i) {
-            acc[i][4 * q + 0] = fmaf(wv[i], dv.x, acc[i][4 * q + 0]);
-            acc[i][4 * q + 1] = fmaf(wv[i], dv.y, acc[i][4 * q + 1]);
-            acc[i][4 * q + 2] = fmaf(wv[i], dv.z, acc[i][4 * q + 2]);
-            acc[i][4 * q + 3] = fmaf(wv[i], dv.w, acc[i][4 * q + 3]);
+            acc[i][4 * q4 + 0] = fmaf(wv[i], dv.x, acc[i][4 * q4 + 0]);
+            acc[i][4 * q4 + 1] = fmaf(wv[i], dv.y, acc[i][4 * q4 + 1]);
+            acc[i][4 * q4 + 2] = fmaf(wv[i], dv.z, acc[i][4 * q4 + 2]);
+            acc[i][4 * q4 + 3] = fmaf(wv[i], dv.w, acc[i][4 * q4 + 3]);
           }
         }
       }
-      __syncthreads();
     }
   }
+  __syncthreads();   // the last chunk's accumulation is done with shared memory
 
   // ---- non-finite rows ----
   // A non-finite channel value reaches every target of a thread that some
@@ -384,15 +444,15 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     }());
     if (any_bad) {
       // the NCG threads of a target group share each row: agree per row
-      if (tid < kTile) row_nf[tid] = 0;
+      if (tid < kTile) S.row_nf[tid] = 0;
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < PB; ++i)
-        if (!isfinite(chk[i])) row_nf[pg * PB + i] = 1;
+        if (!isfinite(chk[i])) S.row_nf[pg * PB + i] = 1;
       __syncthreads();
 #pragma unroll
-      for (int i = 0; i < PB; ++i) row_bad[i] = row_nf[pg * PB + i] != 0;
-      if (tid < kTile && row_nf[tid] && a.tgt_perm[tile * kTile + tid] != 0xffffffffu) {
+      for (int i = 0; i < PB; ++i) row_bad[i] = S.row_nf[pg * PB + i] != 0;
+      if (tid < kTile && S.row_nf[tid] && a.tgt_perm[tile * kTile + tid] != 0xffffffffu) {
         const uint64_t e = (uint64_t)(tile * kTile + tid) * (uint64_t)gridDim.y + blockIdx.y;
         atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
         atomicOr(a.nf_any, 1u);
@@ -422,7 +482,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   }
   // ---- epilogue: weight map and pair count (first channel slab only) ----
   if (blockIdx.y != 0) return;
-  wred[tid] = make_float2(ws, wc);
+  S.wred[tid] = make_float2(ws, wc);
   {
     unsigned c = npair;
 #pragma unroll
@@ -434,7 +494,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     float s = 0.f, c = 0.f;
 #pragma unroll
     for (int q = 0; q < STEP; ++q) {
-      const float2 v = wred[q * kTile + p];
+      const float2 v = S.wred[q * kTile + p];
       const float t = s + v.x;
       const float bp2 = t - s;
       c += (s - (t - bp2)) + (v.x - bp2) + v.y;
@@ -509,10 +569,18 @@ cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s
   constexpr int CPAD = CB * NCG;
   const dim3 grid((unsigned)n_tiles, (unsigned)((a.C + CPAD - 1) / CPAD), (unsigned)a.n_split);
   if (n_tiles == 0) return cudaSuccess;
-  if (dtype == CG_BF16)
-    k_grid_f32<PB, CB, NCG, __nv_bfloat16><<<grid, NTH, 0, s>>>(a);
-  else
-    k_grid_f32<PB, CB, NCG, float><<<grid, NTH, 0, s>>>(a);
+  const size_t smem = sizeof(F32Smem<PB, CB, NCG>);
+  if (dtype == CG_BF16) {
+    auto k = k_grid_f32<PB, CB, NCG, __nv_bfloat16>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTH, smem, s>>>(a);
+  } else {
+    auto k = k_grid_f32<PB, CB, NCG, float>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NTH, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -519,7 +519,10 @@ def time_batched(args, dev, n_jobs=64):
     in {1, 16, 64, 512}, grids 64^2 .. 1024^2, sigma U[1', 8']) replayed as one
     CUDA graph; mixed form = BF16 data for the jobs with C >= 16 and the
     autotuner free to pick the tensor-core form, plain form = FP32 data on
-    the FP32 CUDA-core path (autotuned shapes).  Inputs resident in HBM."""
+    the FP32 CUDA-core path (autotuned shapes).  Each form is timed twice on
+    the same jobs and choices: the per-job graph (one pipeline per job on 16
+    branches) and the fused graph (one sample index and one persistent FP32
+    gridder launch per register shape).  Inputs resident in HBM."""
     import torch
     import workloads
     from paper_1604_06667_gb300 import Batch, Gridder
@@ -536,6 +539,7 @@ def time_batched(args, dev, n_jobs=64):
             forms[form].append((g, lon, lat, d, out))
         keep.append(d32)
     res = {}
+    peaks, _ = load_peaks()
     stream = torch.cuda.current_stream(dev)
     for form, jobs in forms.items():
         b = Batch(jobs, n_streams=16).autotune(reps=2, allow_tc=(form == "mixed")).capture()
@@ -557,6 +561,28 @@ def time_batched(args, dev, n_jobs=64):
                      "updates_per_batch": upd, "pairs_per_batch": int(sum(pairs)),
                      "graph_kernels": b.info()["graph_kernels"],
                      "tc_jobs": sum(1 for c in ch if c["path"] == 2)}
+        # the fused pipeline on the same jobs and choices: one sample index,
+        # one persistent FP32 gridder launch, tensor-core jobs on their own
+        b.set_fused(True).capture()
+        for _ in range(max(3, args.warmup)):
+            b.run()
+        b.sync()
+        e0.record(stream)
+        for _ in range(steps):
+            b.run()
+        e1.record(stream)
+        b.sync()
+        torch.cuda.synchronize()
+        msf = e0.elapsed_time(e1) / steps
+        res[form]["fused"] = {"ms_per_batch": msf, "updates_per_s": upd / (msf / 1e3),
+                              "graph_kernels": b.info()["graph_kernels"]}
+        # the method's bytes of the batch (every job's samples and data read
+        # once, its map and weight map written once) against the HBM peak
+        nbytes = sum(sp["n"] * (16 + sp["C"] * j[3].element_size()) +
+                     sp["side"] ** 2 * (4 * sp["C"] + 4) for sp, j in zip(specs, jobs))
+        best = min(ms, msf)
+        res[form]["bytes_per_batch"] = nbytes
+        res[form]["hbm_frac"] = nbytes / (best / 1e3) / 1e9 / peaks["hbm_gbs"]
         b.close()
     for jobs in forms.values():
         for j in jobs:
@@ -799,7 +825,12 @@ def compact_line(line, detail_file):
         out["batched"] = {"mixed_ms": b["mixed"]["ms_per_batch"],
                           "fp32_ms": b["fp32"]["ms_per_batch"],
                           "ratio": b["mixed_over_fp32"],
-                          "kernels": b["mixed"]["graph_kernels"]}
+                          "kernels": b["mixed"]["graph_kernels"],
+                          "fused_ms": [b["mixed"]["fused"]["ms_per_batch"],
+                                       b["fp32"]["fused"]["ms_per_batch"]],
+                          "fused_kernels": [b["mixed"]["fused"]["graph_kernels"],
+                                            b["fp32"]["fused"]["graph_kernels"]],
+                          "hbm_frac": [b["mixed"]["hbm_frac"], b["fp32"]["hbm_frac"]]}
     if "allsky" in line:
         out["allsky_ms"] = {f: line["allsky"][f]["ms_per_call"] for f in ("bf16", "bf16s", "fp32")
                             if f in line["allsky"]}

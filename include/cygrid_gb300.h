@@ -428,6 +428,35 @@ cg_status cg_batch_get_choice(cg_batch* b, int32_t job, int32_t* path, int32_t* 
 /* Kernels recorded in the captured graph and the number of branches. */
 cg_status cg_batch_info(cg_batch* b, int64_t* graph_kernels, int32_t* n_streams);
 
+/* Choose how the next cg_batch_capture records the batch: fused != 0 builds
+ * one pipeline for all jobs -- one keys pass, one sort of every job's samples
+ * (a composite key keeps each job's samples together, in its own RING key
+ * order), one gather and one candidate-range pass, one persistent FP32
+ * gridder launch per 96 jobs whose CTAs take (job, tile, channel slab,
+ * candidate split) items from a queue ordered by estimated cost, one split
+ * reduction, one non-finite fix-up and one normalisation over all jobs; jobs
+ * whose choice is the tensor-core form (BF16 data, C % 8 == 0, 16-byte
+ * aligned data, [n_targets][C] output) run the tensor-core gridder on their
+ * segment of the shared index.  fused = 0 (the default): one branch per job
+ * as described at cg_batch_create.  Each job computes what cg_grid_oneshot
+ * computes (paper Eq. 1-3); the FP32 results may differ from a one-job call
+ * in the last bits where the candidate splits differ.  While a fused graph
+ * exists the jobs' handles belong to it (their candidate ranges are
+ * rewritten by every replay).  Invalidates a captured graph. */
+cg_status cg_batch_set_fused(cg_batch* b, int32_t fused);
+
+/* Wait for the last cg_batch_run and report the jobs' device errors:
+ * CG_EINVAL (invalid sample coordinates or weights, skipped), CG_ETIMEOUT
+ * (a bounded device wait gave up); the error words are cleared. */
+cg_status cg_batch_sync(cg_batch* b);
+
+/* Testing hook (no paper counterpart): with enable != 0 the fused FP32
+ * gridder's CTAs first wait, for at most wait_cycles SM clock cycles (0: two
+ * million), for a device word that nothing sets, then record ERR_TIMEOUT and
+ * leave without taking items, so that cg_batch_sync reports CG_ETIMEOUT
+ * without a GPU fault.  Invalidates a captured graph. */
+cg_status cg_batch_debug_hold(cg_batch* b, int32_t enable, int64_t wait_cycles);
+
 /* Release the graph, branch streams and events (not the jobs' handles). */
 cg_status cg_batch_destroy(cg_batch* b);
 

@@ -87,6 +87,9 @@ SIGNATURES = {
                             ctypes.POINTER(_dbl), ctypes.POINTER(_i32)],
     "cg_batch_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
     "cg_batch_destroy": [_vp],
+    "cg_batch_set_fused": [_vp, _i32],
+    "cg_batch_sync": [_vp],
+    "cg_batch_debug_hold": [_vp, _i32, _i64],
 }
 
 CG_NOALLOC_MAX_SAMPLES = 262144
@@ -158,6 +161,9 @@ cg_batch_run = _call("cg_batch_run")
 cg_batch_get_choice = _call("cg_batch_get_choice")
 cg_batch_info = _call("cg_batch_info")
 cg_batch_destroy = _call("cg_batch_destroy")
+cg_batch_set_fused = _call("cg_batch_set_fused")
+cg_batch_sync = _call("cg_batch_sync")
+cg_batch_debug_hold = _call("cg_batch_debug_hold")
 
 
 def cg_last_error() -> str:

@@ -2,8 +2,10 @@
 
     b = Batch([(gridder, lon, lat, data, out, out_weights), ...], n_streams=16)
     b.autotune(reps=2)          # per job: FP32 register-blocking shape or BF16 tensor cores
-    b.capture()                 # one graph: fork, every job's one-shot pipeline, join
+    b.set_fused(True)           # optional: one index and one gridder launch for all jobs
+    b.capture()                 # one graph (per-job branches, or the fused pipeline)
     b.run()                     # one launch per replay
+    b.sync()                    # wait; raises on the jobs' device errors
 
 Each job needs its own Gridder (targets, kernel, channel count).  The tensors
 must stay alive and in place while the batch is used: the graph reads and
@@ -62,6 +64,19 @@ class Batch:
 
     def run(self, stream=None):
         C.cg_batch_run(self._h, _stream_handle(stream))
+
+    def set_fused(self, fused: bool = True):
+        C.cg_batch_set_fused(self._h, 1 if fused else 0)
+        return self
+
+    def sync(self):
+        C.cg_batch_sync(self._h)
+
+    def debug_hold(self, enable: bool = True, wait_cycles: int = 0):
+        """Testing hook: the fused FP32 gridder waits for a word nothing
+        sets, gives up and reports a time-out at sync()."""
+        C.cg_batch_debug_hold(self._h, 1 if enable else 0, int(wait_cycles))
+        return self
 
     def choices(self):
         out = []

@@ -237,7 +237,12 @@ cg_status do_add(cg_grid* g, const double* lon, const double* lat, const void* d
     CG_CUDA(grid_tiles_tc(g, data, mode, out, out_w, g->path != CG_PATH_TC_FAST), where);
     if (fused) *fused = fuse;
   } else {
-    CG_CUDA(grid_tiles_f32(g, data, dtype), where);
+    // one-shot calls: the gridder writes R = N / W itself where it can
+    const bool want = out != nullptr && g->acc_empty;
+    bool direct = false;
+    CG_CUDA(grid_tiles_f32(g, data, dtype, want ? out : nullptr, want ? out_w : nullptr, &direct),
+            where);
+    if (fused) *fused = direct;
   }
   cudaEvent_t t4 = tmark(g);
   tstage(g, 0, t0, t1);
@@ -260,7 +265,7 @@ cg_status oneshot_impl(cg_grid* g, const double* lon, const double* lat, const v
   st = do_add(g, lon, lat, data, dtype, weights, n, where, layout_channel_major ? nullptr : out,
               out_w, &fused);
   if (st != CG_OK) return st;
-  if (fused) return CG_OK;  // the tensor-core epilogue already wrote Eq. 3
+  if (fused) return CG_OK;  // the gridder's epilogue already wrote Eq. 3
   st = clear_if_empty(g, where);
   if (st != CG_OK) return st;
   cudaEvent_t t0 = tmark(g);

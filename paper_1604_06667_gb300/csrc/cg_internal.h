@@ -250,15 +250,165 @@ void tiling_free(Tiling& t, cudaStream_t s);
 cudaError_t export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm, int64_t* ring_off,
                          int64_t n);
 
-// k_grid.cu -- the tile gridder (FP32 CUDA-core form).
-cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype);
-constexpr int kF32Configs = 7;
-cg_status batch_fail(cg_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));      // register-blocking shapes of the FP32 gridder
+// k_grid.cu -- the tile gridder (FP32 CUDA-core form).  Arguments of one
+// gridder pass (one job): the t64 tiling, the sorted samples, the data.
+struct GridArgs {
+  const float4* tile_chi;
+  const float4* tile_clo;
+  const float4* tgt_a;
+  const float4* tgt_f1;
+  const float4* tgt_f2;
+  const double2* tgt_ll;
+  const uint32_t* tgt_perm;
+  const int64_t* range_off;
+  const int2* range_s;
+  const float4* s_hi;
+  const float4* s_lo;
+  const uint32_t* perm;
+  const double2* sll;   // FP64 lon/lat of each sample (input order, degrees)
+  const void* data;
+  int C;
+  int vec4;  // data rows are 16-byte (f32) / 8-byte (bf16) aligned in groups of 4
+  KernelDev kd;
+  float* acc_num;
+  float2* acc_w;
+  int accumulate;
+  unsigned long long* pairs;
+  // candidate splits: a tile's candidates are shared by n_split
+  // CTAs that write partial sums, summed by k_split_reduce in split order
+  const int32_t* tile_cand;
+  int n_split;
+  int64_t n_slots;
+  float* part_num;      // [n_split][slots][C]
+  float2* part_w;       // [n_split][slots]
+  // rows with a non-finite numerator (bit slot * n_slabs + slab)
+  uint32_t* nf_bits;
+  uint32_t* nf_any;
+  // one-shot output (no candidate splits, no accumulation): R = N / W
+  // written straight into the caller's [P][C] map and W into out_w (if
+  // set); null: numerator and W into the accumulators
+  float* out;
+  float* out_w;
+};
+// out != null (one-shot call, pixel-major map): R = N / W straight into out
+// when the pass has no candidate splits (*direct = true), else the
+// accumulators as usual.
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, float* out = nullptr,
+                           float* out_w = nullptr, bool* direct = nullptr);
+constexpr int kF32Configs = 7;   // register-blocking shapes of the FP32 gridder
 int f32_default_config(int C);
 // the same into given accumulators; dscale != 0 evaluates w d^2 dscale
 // instead of w (the d/dsigma pass) and counts no pairs
 cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
-                              float2* acc_w, int accumulate, float dscale, int C = -1);
+                              float2* acc_w, int accumulate, float dscale, int C = -1,
+                              float* out = nullptr, float* out_w = nullptr,
+                              bool* direct = nullptr);
+cg_status batch_fail(cg_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
+// ---- fused batches: one sample index for all jobs (k_healpix.cu) --------
+// The samples of all jobs sorted together by a composite key: the job's key
+// base (the RING index ranges of the jobs before it, each npix + 1 long) plus
+// the sample's RING index at the job's nside, so that every job's samples
+// form one segment of the sorted order, in the job's own key order.
+struct BatchIndexJob {
+  const double* lon;
+  const double* lat;
+  const float* weights;
+  int64_t n;              // samples
+  int64_t off;            // first position of the job in the batch sample arrays
+  int64_t nside;
+  int lg;                 // log2 nside (-1: not a power of two)
+  uint64_t key_base;
+  int64_t ring_base;      // first of the job's 4 nside + 1 ring offsets
+  // the tiling of the job's gridder form: its candidate ranges are written
+  const Range* ranges;
+  const int64_t* range_off;
+  int64_t n_tiles;
+  int2* range_s;
+  int32_t* range_c;
+  int32_t* tile_cand;
+};
+struct BatchIndex {
+  int n_jobs = 0;
+  int64_t N = 0;                    // samples of all jobs
+  int64_t n_ring = 0;               // ring offsets of all jobs
+  int64_t n_tiles = 0;              // tiles of all jobs
+  int key_bits = 0;
+  BatchIndexJob* jobs = nullptr;    // device [n_jobs]
+  int64_t* key_blk = nullptr;       // device [n_jobs + 1]: prefix of ceil(n / 256)
+  int64_t n_key_blk = 0;
+  int64_t* gth_blk = nullptr;       // device [n_jobs + 1]: prefix of ceil((n + 1) / 256)
+  int64_t n_gth_blk = 0;
+  int64_t* tile_off = nullptr;      // device [n_jobs + 1]: prefix of n_tiles
+  uint64_t* key = nullptr;          // [N] composite keys, input order
+  uint32_t* val = nullptr;          // [N] the sample's index within its job
+  float4* u_hi = nullptr;           // [N] input order
+  float4* u_lo = nullptr;
+  double2* sll = nullptr;
+  float4* s_hi = nullptr;           // [N] sorted order
+  float4* s_lo = nullptr;
+  uint32_t* skey = nullptr;         // [N] sorted RING keys (the job's own)
+  int32_t* ring_off = nullptr;      // [n_ring] relative to the job's segment
+  uint64_t* sorted_key = nullptr;   // set by the sort
+  uint32_t* sorted_val = nullptr;
+  SortWork sw;
+};
+// Allocate the sample arrays (jobs, prefixes and sizes set by the caller).
+cudaError_t batch_index_alloc(BatchIndex& bi, cudaStream_t s);
+// keys, one sort, gather + ring offsets, every job's candidate ranges
+cudaError_t batch_index_run(BatchIndex& bi, unsigned* err, cudaStream_t s, int64_t* launches);
+void batch_index_free(BatchIndex& bi, cudaStream_t s);
+
+// ---- fused batches: one FP32 gridder launch for all jobs (k_grid.cu) ----
+// Items (job, tile, channel slab, candidate split) are taken from a queue
+// ordered by decreasing estimated cost; one launch per register-blocking
+// shape of the one-job gridder (by channel count, or the autotuner's choice)
+// and up to kF32MultiMaxJobs jobs.
+constexpr int kF32MultiShapes = kF32Configs;
+constexpr int kF32MultiMaxJobs = 96;  // jobs per launch (their arguments fill the parameter space)
+int f32_multi_shape(int C);           // default shape for C channels (f32_default_config)
+int f32_multi_cpad(int shape);        // channels per slab of a shape
+struct F32MultiJob {
+  GridArgs a;
+  int shape;
+  int dtype;
+  int n_slabs;
+  int pad;                            // channels per slab of the shape
+};
+struct F32Multi {
+  int shape = 0;                      // the register-blocking shape of all its jobs
+  F32MultiJob* jobs = nullptr;        // device [n_jobs]
+  const F32MultiJob* hjobs = nullptr; // host copy (the launcher reads it)
+  int n_jobs = 0;
+  int64_t* item_off = nullptr;        // device [n_jobs + 1]: prefix of items
+  int64_t n_items = 0;
+  int32_t* order = nullptr;           // device [n_items]: items, costliest first
+  unsigned* head = nullptr;           // queue head (cleared by the order pass)
+  unsigned* err = nullptr;
+  const int* hold = nullptr;          // testing hook: a word nothing sets
+  long long hold_cycles = 0;
+  // split reduction, normalisation and non-finite fix-up of all jobs
+  struct Out {
+    float* out;                       // caller's map
+    float* out_w;
+    int channel_major;
+    int vec4;                         // [P][C], C % 4 == 0, 16-byte aligned map
+    int64_t P;
+  };
+  Out* outs = nullptr;                // device [n_jobs]
+  // CTAs of the normalisation (every job) and of the split reduction (jobs
+  // with candidate splits): prefix over the jobs of their CTA counts
+  int64_t* fin_blk = nullptr;         // device [n_jobs + 1]
+  int64_t n_fin_blk = 0;
+  int64_t* red_blk = nullptr;         // device [n_jobs + 1]
+  int64_t n_red_blk = 0;
+  int64_t* word_off = nullptr;        // device [n_jobs + 1]: prefix of bitmap words
+  int64_t n_words = 0;
+  uint32_t* nf_any = nullptr;
+};
+cudaError_t grid_f32_multi(const F32Multi& m, cudaStream_t s, int64_t* launches);
+constexpr int kMultiFinElems = 1024;  // map values per CTA of the normalisation
+constexpr int kMultiRedElems = 256;   // values per CTA of the split reduction
 // k_grid_tc.cu -- the tile gridder, BF16 tcgen05 form (TMEM accumulators).
 // mode 0: store into the accumulators, 1: add into them, 2: one-shot
 // normalised output in the caller's [P][C] layout (out, out_w).

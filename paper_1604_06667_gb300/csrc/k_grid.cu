@@ -22,6 +22,8 @@
 // thread's other targets through 0 x NaN) is left to k_nonfinite_fixup.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "cg_common.cuh"
 #include "cg_cut.cuh"
 #include "cg_internal.h"
@@ -31,39 +33,6 @@ namespace {
 
 constexpr int kRangeBatch = 256;
 
-struct GridArgs {
-  const float4* tile_chi;
-  const float4* tile_clo;
-  const float4* tgt_a;
-  const float4* tgt_f1;
-  const float4* tgt_f2;
-  const double2* tgt_ll;
-  const uint32_t* tgt_perm;
-  const int64_t* range_off;
-  const int2* range_s;
-  const float4* s_hi;
-  const float4* s_lo;
-  const uint32_t* perm;
-  const double2* sll;   // FP64 lon/lat of each sample (input order, degrees)
-  const void* data;
-  int C;
-  int vec4;  // data rows are 16-byte (f32) / 8-byte (bf16) aligned in groups of 4
-  KernelDev kd;
-  float* acc_num;
-  float2* acc_w;
-  int accumulate;
-  unsigned long long* pairs;
-  // candidate splits (blockIdx.z): a tile's candidates are shared by n_split
-  // CTAs that write partial sums, summed by k_split_reduce in split order
-  const int32_t* tile_cand;
-  int n_split;
-  int64_t n_slots;
-  float* part_num;      // [n_split][slots][C]
-  float2* part_w;       // [n_split][slots]
-  // rows with a non-finite numerator (bit slot * gridDim.y + blockIdx.y)
-  uint32_t* nf_bits;
-  uint32_t* nf_any;
-};
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -156,6 +125,7 @@ struct alignas(16) F32Smem {
   int2 rg[kRangeBatch];          // a batch of the tile's sample ranges
   int rg_pre[kRangeBatch + 1];   // candidates before each range of the batch
   float2 wred[NTH];
+  float wfin[kTile];             // W of the tile's targets (one-shot output)
   int row_nf[kTile];             // rows of this CTA with a non-finite numerator
 };
 
@@ -172,9 +142,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// PB targets x CB channels per thread in phase B; NCG channel groups.
+// One (tile, channel slab, candidate split) item of the FP32 gridder, by a
+// CTA of (kTile / PB) * NCG threads: PB targets x CB channels per thread in
+// phase B, NCG channel groups.
 template <int PB, int CB, int NCG, typename DT>
-__global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
+__device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB, NCG>& S,
+                                              int64_t tile, int slab, int split, int n_slabs) {
   using Smem = F32Smem<PB, CB, NCG>;
   constexpr int NTH = Smem::NTH;
   constexpr int CPAD = Smem::CPAD;
@@ -182,12 +155,9 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   constexpr int STEP = NTH / kTile;
   static_assert(NTH % kTile == 0, "threads must cover the tile");
   static_assert(CB % 4 == 0, "channel blocks are float4 wide");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
 
   const int tid = threadIdx.x;
-  const int64_t tile = blockIdx.x;
-  const int c_base = blockIdx.y * CPAD;
+  const int c_base = slab * CPAD;
 
   // phase-A identity: one target, every STEP-th candidate
   const int p = tid % kTile;
@@ -224,7 +194,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
   if (a.n_split > 1) {
     const int total_t = a.tile_cand[tile];
     const int per = ((total_t + a.n_split - 1) / a.n_split + K - 1) / K * K;
-    c_lo = (int)blockIdx.z * per;
+    c_lo = split * per;
     c_hi = min(total_t, c_lo + per);
   }
   int cbase = 0;   // the tile's candidates before the current range batch
@@ -453,7 +423,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
 #pragma unroll
       for (int i = 0; i < PB; ++i) row_bad[i] = S.row_nf[pg * PB + i] != 0;
       if (tid < kTile && S.row_nf[tid] && a.tgt_perm[tile * kTile + tid] != 0xffffffffu) {
-        const uint64_t e = (uint64_t)(tile * kTile + tid) * (uint64_t)gridDim.y + blockIdx.y;
+        const uint64_t e = (uint64_t)(tile * kTile + tid) * (uint64_t)n_slabs + (uint64_t)slab;
         atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
         atomicOr(a.nf_any, 1u);
       }
@@ -463,15 +433,59 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     }
   }
 
+  if (a.out) {
+    // ---- one-shot epilogue: R = N / W (paper Eq. 3) straight into the
+    // caller's [P][C] map; every slab's CTA holds all of the tile's weights
+    S.wred[tid] = make_float2(ws, wc);
+    if (slab == 0) {
+      unsigned c = npair;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if ((tid & 31) == 0 && c && a.pairs) atomicAdd(a.pairs, (unsigned long long)c);
+    }
+    __syncthreads();
+    if (kk0 == 0) {
+      float s = 0.f, c = 0.f;
+#pragma unroll
+      for (int q = 0; q < STEP; ++q) {
+        const float2 v = S.wred[q * kTile + p];
+        const float t = s + v.x;
+        const float bp2 = t - s;
+        c += (s - (t - bp2)) + (v.x - bp2) + v.y;
+        s = t;
+      }
+      S.wfin[p] = s + c;
+      const uint32_t u = a.tgt_perm[slot];
+      if (slab == 0 && a.out_w && u != 0xffffffffu) a.out_w[u] = s + c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      const int64_t sl = tile * kTile + pg * PB + i;
+      const uint32_t u = a.tgt_perm[sl];
+      if (u == 0xffffffffu || row_bad[i]) continue;
+      const float W = S.wfin[pg * PB + i];
+      float* dst = a.out + (size_t)u * C;
+#pragma unroll
+      for (int q = 0; q < CB / 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c_base + 4 * cg + 4 * NCG * q + j;
+          if (c < C) dst[c] = (W > 0.f) ? acc[i][4 * q + j] / W : __int_as_float(0x7fc00000);
+        }
+    }
+    return;
+  }
+
   // ---- epilogue: numerator ----
-  const bool split = a.n_split > 1;
+  const bool splits = a.n_split > 1;
 #pragma unroll
   for (int i = 0; i < PB; ++i) {
     const int64_t sl = tile * kTile + pg * PB + i;
     if (a.tgt_perm[sl] == 0xffffffffu || row_bad[i]) continue;
-    float* dst = split ? a.part_num + ((size_t)blockIdx.z * a.n_slots + sl) * C
-                       : a.acc_num + (size_t)sl * C;
-    const bool add = a.accumulate && !split;
+    float* dst = splits ? a.part_num + ((size_t)split * a.n_slots + sl) * C
+                        : a.acc_num + (size_t)sl * C;
+    const bool add = a.accumulate && !splits;
 #pragma unroll
     for (int q = 0; q < CB / 4; ++q)
 #pragma unroll
@@ -481,7 +495,7 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
       }
   }
   // ---- epilogue: weight map and pair count (first channel slab only) ----
-  if (blockIdx.y != 0) return;
+  if (slab != 0) return;
   S.wred[tid] = make_float2(ws, wc);
   {
     unsigned c = npair;
@@ -500,8 +514,8 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
       c += (s - (t - bp2)) + (v.x - bp2) + v.y;
       s = t;
     }
-    if (split) {
-      a.part_w[(size_t)blockIdx.z * a.n_slots + slot] = make_float2(s, c);
+    if (splits) {
+      a.part_w[(size_t)split * a.n_slots + slot] = make_float2(s, c);
       return;
     }
     float2 old = a.accumulate ? a.acc_w[slot] : make_float2(0.f, 0.f);
@@ -510,6 +524,13 @@ __global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(GridArgs a) {
     const float err = (old.x - (t - bp2)) + (s - bp2);
     a.acc_w[slot] = make_float2(t, old.y + c + err);
   }
+}
+
+template <int PB, int CB, int NCG, typename DT>
+__global__ void __launch_bounds__((kTile / PB) * NCG) k_grid_f32(const __grid_constant__ GridArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& S = *reinterpret_cast<F32Smem<PB, CB, NCG>*>(smem_raw);
+  grid_item_f32<PB, CB, NCG, DT>(a, S, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.y);
 }
 
 // Sum the candidate-split partials in split order into the accumulators.
@@ -586,9 +607,10 @@ cudaError_t launch(const GridArgs& a, int64_t n_tiles, int dtype, cudaStream_t s
 
 // One FP32 gridder pass: choose the candidate splits, grow the partial-sum
 // scratch if needed, launch, reduce the splits, and compute the flagged
-// non-finite rows again.
+// non-finite rows again.  A one-shot output (a.out) is kept only without
+// candidate splits; *direct tells whether the map was written.
 template <int PB, int CB, int NCG>
-cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
+cudaError_t run(cg_grid* g, GridArgs& a, int dtype, bool* direct) {
   constexpr int CPAD = CB * NCG;
   const int64_t nt = g->t64.n_tiles;
   cudaStream_t s = g->stream;
@@ -598,6 +620,11 @@ cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
   a.n_split = splits_for<PB, CB, NCG>(nt, a.C, nsm);
   a.part_num = nullptr;
   a.part_w = nullptr;
+  if (a.n_split > 1 || a.accumulate) {
+    a.out = nullptr;
+    a.out_w = nullptr;
+  }
+  if (direct) *direct = a.out != nullptr;
   if (a.n_split > 1) {
     const size_t need_n = (size_t)a.n_split * (size_t)g->n_slots * (size_t)a.C;
     const size_t need_w = (size_t)a.n_split * (size_t)g->n_slots;
@@ -640,8 +667,8 @@ cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
   rows.C = a.C;
   rows.cp = CPAD;
   rows.n_slabs = n_slabs;
-  rows.mode = a.accumulate ? 1 : 0;
-  rows.out = nullptr;
+  rows.mode = a.out ? 2 : (a.accumulate ? 1 : 0);
+  rows.out = a.out;
   rows.acc_num = a.acc_num;
   rows.kd = a.kd;
   return nonfinite_fixup(g, rows);
@@ -649,14 +676,20 @@ cudaError_t run(cg_grid* g, GridArgs& a, int dtype) {
 
 }  // namespace
 
-cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype) {
-  return grid_tiles_f32_to(g, data, dtype, g->acc_num, g->acc_w, g->acc_empty ? 0 : 1, 0.f);
+cudaError_t grid_tiles_f32(cg_grid* g, const void* data, int dtype, float* out, float* out_w,
+                           bool* direct) {
+  return grid_tiles_f32_to(g, data, dtype, g->acc_num, g->acc_w, g->acc_empty ? 0 : 1, 0.f, -1,
+                           out, out_w, direct);
 }
 
 cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* acc_num,
-                              float2* acc_w, int accumulate, float dscale, int C) {
+                              float2* acc_w, int accumulate, float dscale, int C, float* out,
+                              float* out_w, bool* direct) {
+  if (direct) *direct = false;
   if (C < 0) C = g->C;
   GridArgs a;
+  a.out = out;
+  a.out_w = out_w;
   a.tile_chi = g->t64.chi;
   a.tile_clo = g->t64.clo;
   a.tgt_a = g->t64.a;
@@ -686,13 +719,13 @@ cudaError_t grid_tiles_f32_to(cg_grid* g, const void* data, int dtype, float* ac
   int cfg = g->f32_cfg;
   if (cfg < 0 || cfg >= kF32Configs || C != g->C) cfg = f32_default_config(C);
   switch (cfg) {
-    case 0: return run<1, 4, 1>(g, a, dtype);
-    case 1: return run<1, 8, 1>(g, a, dtype);
-    case 2: return run<1, 8, 2>(g, a, dtype);
-    case 3: return run<2, 8, 4>(g, a, dtype);
-    case 4: return run<2, 16, 4>(g, a, dtype);
-    case 5: return run<4, 16, 8>(g, a, dtype);
-    default: return run<4, 16, 16>(g, a, dtype);
+    case 0: return run<1, 4, 1>(g, a, dtype, direct);
+    case 1: return run<1, 8, 1>(g, a, dtype, direct);
+    case 2: return run<1, 8, 2>(g, a, dtype, direct);
+    case 3: return run<2, 8, 4>(g, a, dtype, direct);
+    case 4: return run<2, 16, 4>(g, a, dtype, direct);
+    case 5: return run<4, 16, 8>(g, a, dtype, direct);
+    default: return run<4, 16, 16>(g, a, dtype, direct);
   }
 }
 
@@ -740,87 +773,95 @@ __device__ __forceinline__ float fix_load(const FixArgs& a, size_t i) {
                 : static_cast<const float*>(a.data)[i];
 }
 
-__global__ void __launch_bounds__(kFixThreads) k_nonfinite_fixup(FixArgs a) {
-  __shared__ float w_s[kFixThreads];
-  __shared__ uint32_t idx_s[kFixThreads];
-  __shared__ double wsum_s[kFixThreads];
-  __shared__ uint32_t word_s;
-  if (*a.any == 0u) return;   // the common case: nothing flagged
+struct FixShared {
+  float w[kFixThreads];
+  uint32_t idx[kFixThreads];
+  double wsum[kFixThreads];
+  uint32_t word;
+};
+
+// The flagged rows of bitmap word wd (the whole CTA; clears the word).
+__device__ __forceinline__ void fix_word(const FixArgs& a, int64_t wd, FixShared& F) {
   const int tid = threadIdx.x;
-  for (int64_t wd = blockIdx.x; wd < a.n_words; wd += gridDim.x) {
-    __syncthreads();
-    if (tid == 0) word_s = a.bits[wd];
-    __syncthreads();
-    uint32_t bits = word_s;
-    while (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int64_t e = wd * 32 + b;
-      const int64_t slot = e / a.n_slabs;
-      const int slab = (int)(e % a.n_slabs);
-      const int64_t tile = slot / a.T;
-      const float4 at = a.ta[slot];
-      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
-      if (a.kd.type == CG_GAUSS2D) {
-        f1 = a.f1[slot];
-        f2 = a.f2[slot];
-      }
-      const float4 chi = a.chi[tile], clo = a.clo[tile];
-      const int c = slab * a.cp + tid;
-      const bool mine = tid < a.cp && c < a.C;
-      float acc = 0.f;
-      double wsum = 0.0;
-      for (int64_t r = a.range_off[tile]; r < a.range_off[tile + 1]; ++r) {
-        const int2 rg = a.range_s[r];
-        for (int j0 = rg.x; j0 < rg.y; j0 += kFixThreads) {
-          __syncthreads();
-          const int pos = j0 + tid;
-          float w = -0.f;
-          uint32_t idx = 0;
-          if (pos < rg.y) {
-            const float4 h = a.s_hi[pos], l = a.s_lo[pos];
-            const float4 sh = make_float4(df_diff(h.x, l.x, chi.x, clo.x),
-                                          df_diff(h.y, l.y, chi.y, clo.y),
-                                          df_diff(h.z, l.z, chi.z, clo.z), h.w);
-            idx = a.perm[pos];
-            bool in;
-            w = pair_weight(a.kd, at, f1, f2, sh, a.tll[slot], a.sll, idx, in);
-            if (in) wsum += (double)w;
-          }
-          w_s[tid] = w;
-          idx_s[tid] = idx;
-          __syncthreads();
-          const int n = min(kFixThreads, rg.y - j0);
-          if (mine)
-            for (int k = 0; k < n; ++k)
-              if (takes_part(w_s[k])) acc = fmaf(w_s[k], fix_load(a, (size_t)idx_s[k] * a.C + c), acc);
-        }
-      }
-      double W = 0.0;
-      if (a.mode == 2) {
-        wsum_s[tid] = wsum;
+  __syncthreads();
+  if (tid == 0) F.word = a.bits[wd];
+  __syncthreads();
+  uint32_t bits = F.word;
+  if (!bits) return;
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const int64_t e = wd * 32 + b;
+    const int64_t slot = e / a.n_slabs;
+    const int slab = (int)(e % a.n_slabs);
+    const int64_t tile = slot / a.T;
+    const float4 at = a.ta[slot];
+    float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
+    if (a.kd.type == CG_GAUSS2D) {
+      f1 = a.f1[slot];
+      f2 = a.f2[slot];
+    }
+    const float4 chi = a.chi[tile], clo = a.clo[tile];
+    const int c = slab * a.cp + tid;
+    const bool mine = tid < a.cp && c < a.C;
+    float acc = 0.f;
+    double wsum = 0.0;
+    for (int64_t r = a.range_off[tile]; r < a.range_off[tile + 1]; ++r) {
+      const int2 rg = a.range_s[r];
+      for (int j0 = rg.x; j0 < rg.y; j0 += kFixThreads) {
         __syncthreads();
-        for (int o = kFixThreads / 2; o > 0; o >>= 1) {
-          if (tid < o) wsum_s[tid] += wsum_s[tid + o];
-          __syncthreads();
+        const int pos = j0 + tid;
+        float w = -0.f;
+        uint32_t idx = 0;
+        if (pos < rg.y) {
+          const float4 h = a.s_hi[pos], l = a.s_lo[pos];
+          const float4 sh = make_float4(df_diff(h.x, l.x, chi.x, clo.x),
+                                        df_diff(h.y, l.y, chi.y, clo.y),
+                                        df_diff(h.z, l.z, chi.z, clo.z), h.w);
+          idx = a.perm[pos];
+          bool in;
+          w = pair_weight(a.kd, at, f1, f2, sh, a.tll[slot], a.sll, idx, in);
+          if (in) wsum += (double)w;
         }
-        W = wsum_s[0];
-      }
-      if (mine) {
-        if (a.mode == 2) {
-          const uint32_t user = a.perm_t[slot];
-          if (user != 0xffffffffu)
-            a.out[(size_t)user * a.C + c] = (W > 0.0) ? (float)((double)acc / W) : __int_as_float(0x7fc00000);
-        } else if (a.mode == 1) {
-          a.acc_num[(size_t)slot * a.C + c] += acc;
-        } else {
-          a.acc_num[(size_t)slot * a.C + c] = acc;
-        }
+        F.w[tid] = w;
+        F.idx[tid] = idx;
+        __syncthreads();
+        const int n = min(kFixThreads, rg.y - j0);
+        if (mine)
+          for (int k = 0; k < n; ++k)
+            if (takes_part(F.w[k])) acc = fmaf(F.w[k], fix_load(a, (size_t)F.idx[k] * a.C + c), acc);
       }
     }
-    __syncthreads();
-    if (tid == 0 && word_s) a.bits[wd] = 0u;
+    double W = 0.0;
+    if (a.mode == 2) {
+      F.wsum[tid] = wsum;
+      __syncthreads();
+      for (int o = kFixThreads / 2; o > 0; o >>= 1) {
+        if (tid < o) F.wsum[tid] += F.wsum[tid + o];
+        __syncthreads();
+      }
+      W = F.wsum[0];
+    }
+    if (mine) {
+      if (a.mode == 2) {
+        const uint32_t user = a.perm_t[slot];
+        if (user != 0xffffffffu)
+          a.out[(size_t)user * a.C + c] = (W > 0.0) ? (float)((double)acc / W) : __int_as_float(0x7fc00000);
+      } else if (a.mode == 1) {
+        a.acc_num[(size_t)slot * a.C + c] += acc;
+      } else {
+        a.acc_num[(size_t)slot * a.C + c] = acc;
+      }
+    }
   }
+  __syncthreads();
+  if (tid == 0) a.bits[wd] = 0u;
+}
+
+__global__ void __launch_bounds__(kFixThreads) k_nonfinite_fixup(FixArgs a) {
+  __shared__ FixShared F;
+  if (*a.any == 0u) return;   // the common case: nothing flagged
+  for (int64_t wd = blockIdx.x; wd < a.n_words; wd += gridDim.x) fix_word(a, wd, F);
 }
 
 }  // namespace
@@ -875,6 +916,346 @@ cudaError_t nonfinite_fixup(cg_grid* g, const NonfiniteRows& j) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   k_nonfinite_fixup<<<(unsigned)nsm, kFixThreads, 0, g->stream>>>(a);
   g->n_launches += 1;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused batches: one FP32 gridder launch for the items of all jobs.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kMultiBins = 256;
+constexpr int kOrderCta = 1024;
+
+// Largest j with off[j] <= x (off[0] = 0, off non-decreasing, x < off[n]).
+__device__ __forceinline__ int find_job(const int64_t* __restrict__ off, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct ItemPos {
+  int job;
+  int64_t tile;
+  int slab, split, n_slabs;
+};
+
+__device__ __forceinline__ ItemPos decode_item(const F32Multi& m, int64_t it) {
+  ItemPos q;
+  q.job = find_job(m.item_off, m.n_jobs, it);
+  const F32MultiJob& J = m.jobs[q.job];
+  const int64_t local = it - m.item_off[q.job];
+  const int ns = J.a.n_split, nb = J.n_slabs;
+  q.n_slabs = nb;
+  q.tile = local / ((int64_t)nb * ns);
+  const int r = (int)(local - q.tile * nb * ns);
+  q.slab = r / ns;
+  q.split = r % ns;
+  return q;
+}
+
+// Decreasing estimated cost (weights of the tile's share of candidates plus
+// its channel work), in log-spaced bins.
+__device__ __forceinline__ int multi_bin(const F32Multi& m, int64_t it) {
+  const ItemPos q = decode_item(m, it);
+  const F32MultiJob& J = m.jobs[q.job];
+  const int ns = J.a.n_split;
+  const float cand = (float)((J.a.tile_cand[q.tile] + ns - 1) / ns);
+  const float cost = cand * (float)(kTile + J.pad);
+  const int b = (int)(8.f * __log2f(1.f + cost));
+  return kMultiBins - 1 - min(max(b, 0), kMultiBins - 1);
+}
+
+// One CTA: the queue order (counting sort by cost bin), and the queue head
+// and the non-finite flag cleared for the gridder launch that follows.
+__global__ void __launch_bounds__(kOrderCta) k_multi_order(const __grid_constant__ F32Multi m) {
+  __shared__ int32_t cnt[kMultiBins];
+  __shared__ int32_t wsum[kOrderCta / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    *m.head = 0u;
+    *m.nf_any = 0u;
+  }
+  for (int i = tid; i < kMultiBins; i += kOrderCta) cnt[i] = 0;
+  __syncthreads();
+  for (int64_t it = tid; it < m.n_items; it += kOrderCta) atomicAdd(&cnt[multi_bin(m, it)], 1);
+  __syncthreads();
+  // exclusive scan of the bins (one per thread of the first kMultiBins)
+  const int v = tid < kMultiBins ? cnt[tid] : 0;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  if (tid < kMultiBins) cnt[tid] = incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+  __syncthreads();
+  for (int64_t it = tid; it < m.n_items; it += kOrderCta) {
+    const int pos = atomicAdd(&cnt[multi_bin(m, it)], 1);
+    m.order[pos] = (int32_t)it;
+  }
+}
+
+template <int PB, int CB, int NCG>
+__device__ __forceinline__ void multi_item(const GridArgs& a, unsigned char* raw, int dtype,
+                                           const ItemPos& q) {
+  auto& S = *reinterpret_cast<F32Smem<PB, CB, NCG>*>(raw);
+  if (dtype == CG_BF16)
+    grid_item_f32<PB, CB, NCG, __nv_bfloat16>(a, S, q.tile, q.slab, q.split, q.n_slabs);
+  else
+    grid_item_f32<PB, CB, NCG, float>(a, S, q.tile, q.slab, q.split, q.n_slabs);
+}
+
+// The gridder launch carries every job's arguments in its parameter space, so
+// that the items read them as constant operands (like a one-job launch).
+struct MultiLaunch {
+  F32Multi m;
+  GridArgs ga[kF32MultiMaxJobs];
+};
+
+// Persistent CTAs take items from the queue until it is empty.  One kernel
+// per register-blocking shape of the one-job gridder (the jobs of a launch
+// share it), held to the one-job kernel's CTAs per SM (MINB); as many CTAs as
+// fit on the GPU.
+template <int PB, int CB, int NCG, int MINB>
+__global__ void __launch_bounds__((kTile / PB) * NCG, MINB)
+    k_grid_f32_multi(const __grid_constant__ MultiLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const F32Multi& m = L.m;
+  __shared__ int64_t s_item;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_stop = 0;
+    if (m.hold) {
+      // testing hook: wait for a word that nothing sets; the wait runs out
+      // and the CTA leaves without taking an item
+      const long long t0 = clock64();
+      while (*((volatile const int*)m.hold) == 0 && clock64() - t0 < m.hold_cycles) __nanosleep(1000);
+      if (*((volatile const int*)m.hold) == 0) {
+        set_error(m.err, ERR_TIMEOUT);
+        s_stop = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned q = atomicAdd(m.head, 1u);
+      s_item = (int64_t)q < m.n_items ? (int64_t)m.order[q] : -1;
+    }
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it < 0) break;
+    const ItemPos q = decode_item(m, it);
+    const int dtype = m.jobs[q.job].dtype;
+    const GridArgs& ja = L.ga[__shfl_sync(0xffffffffu, q.job, 0)];
+    multi_item<PB, CB, NCG>(ja, smem_raw, dtype, q);
+    __syncthreads();   // the item is done with s_item and shared memory
+  }
+}
+
+// Candidate-split partials of every split job, in split order, into its
+// accumulators; rows flagged as non-finite are left to the fix-up.  CTA b
+// serves kMultiRedElems values of the job whose CTA range holds b: the
+// numerator [slots][C], then the weight map [slots].
+__global__ void __launch_bounds__(kMultiRedElems) k_multi_reduce(const __grid_constant__ F32Multi m) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = find_job(m.red_blk, m.n_jobs, blockIdx.x);
+  __syncthreads();
+  const int job = s_job;
+  const F32MultiJob& J = m.jobs[job];
+  const int ns = J.a.n_split;
+  const int C = J.a.C;
+  const int64_t n_slots = J.a.n_slots;
+  const int64_t le = (int64_t)(blockIdx.x - m.red_blk[job]) * kMultiRedElems + threadIdx.x;
+  if (le < n_slots * C) {
+    const int64_t sl = le / C;
+    if (J.a.tgt_perm[sl] == 0xffffffffu) return;
+    const uint64_t b = (uint64_t)sl * (uint64_t)J.n_slabs + (uint64_t)((le - sl * C) / J.pad);
+    if ((J.a.nf_bits[b >> 5] >> (b & 31)) & 1u) return;
+    float v = 0.f;
+    for (int z = 0; z < ns; ++z) v += J.a.part_num[(size_t)z * n_slots * C + le];
+    J.a.acc_num[le] = v;
+    return;
+  }
+  const int64_t sl = le - n_slots * C;
+  if (sl >= n_slots || J.a.tgt_perm[sl] == 0xffffffffu) return;
+  float s = 0.f, c = 0.f;
+  for (int z = 0; z < ns; ++z) {
+    const float2 v = J.a.part_w[(size_t)z * n_slots + sl];
+    const float t = s + v.x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v.x - bp) + v.y;
+    s = t;
+  }
+  J.a.acc_w[sl] = make_float2(s, c);
+}
+
+// The flagged rows of all jobs (bitmap words of all jobs, grid-stride).
+__global__ void __launch_bounds__(kFixThreads) k_multi_fixup(const __grid_constant__ F32Multi m) {
+  __shared__ FixShared F;
+  if (*m.nf_any == 0u) return;
+  for (int64_t gw = blockIdx.x; gw < m.n_words; gw += gridDim.x) {
+    const int job = find_job(m.word_off, m.n_jobs, gw);
+    const F32MultiJob& J = m.jobs[job];
+    const int64_t wd = gw - m.word_off[job];
+    if (J.a.nf_bits[wd] == 0u) continue;   // the same word for every thread
+    FixArgs f;
+    f.chi = J.a.tile_chi;
+    f.clo = J.a.tile_clo;
+    f.ta = J.a.tgt_a;
+    f.range_off = J.a.range_off;
+    f.range_s = J.a.range_s;
+    f.T = kTile;
+    f.f1 = J.a.tgt_f1;
+    f.f2 = J.a.tgt_f2;
+    f.tll = J.a.tgt_ll;
+    f.s_hi = J.a.s_hi;
+    f.s_lo = J.a.s_lo;
+    f.perm = J.a.perm;
+    f.sll = J.a.sll;
+    f.kd = J.a.kd;
+    f.data = J.a.data;
+    f.bf16 = J.dtype == CG_BF16;
+    f.C = J.a.C;
+    f.cp = J.pad;
+    f.n_slabs = J.n_slabs;
+    f.mode = J.a.out ? 2 : 0;
+    f.out = J.a.out;
+    f.acc_num = J.a.acc_num;
+    f.perm_t = J.a.tgt_perm;
+    f.bits = J.a.nf_bits;
+    f.any = m.nf_any;
+    f.n_words = 0;
+    fix_word(f, wd, F);
+  }
+}
+
+// Eq. 3 for every job: R = N / W (NaN where W = 0) in the caller's layout.
+// CTA b serves kMultiFinElems numerator values of the job whose CTA range
+// holds b, four consecutive channels of one target per thread where the
+// map allows 16-byte rows.
+__global__ void __launch_bounds__(256) k_multi_finalize(const __grid_constant__ F32Multi m) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = find_job(m.fin_blk, m.n_jobs, blockIdx.x);
+  __syncthreads();
+  const int job = s_job;
+  const F32MultiJob& J = m.jobs[job];
+  const F32Multi::Out o = m.outs[job];
+  const int C = J.a.C;
+  const int64_t n = J.a.n_slots * C;
+  const int64_t base = (int64_t)(blockIdx.x - m.fin_blk[job]) * kMultiFinElems;
+  if (o.vec4) {
+    const int64_t e = base + 4 * (int64_t)threadIdx.x;
+    if (e >= n) return;
+    const int64_t slot = e / C;
+    const int c = (int)(e - slot * C);
+    const uint32_t u = J.a.tgt_perm[slot];
+    if (u == 0xffffffffu) return;
+    const float2 w2 = J.a.acc_w[slot];
+    const float W = w2.x + w2.y;
+    const float4 v = *reinterpret_cast<const float4*>(J.a.acc_num + e);
+    float4 r;
+    if (W > 0.f) {
+      r = make_float4(v.x / W, v.y / W, v.z / W, v.w / W);
+    } else {
+      const float q = __int_as_float(0x7fc00000);
+      r = make_float4(q, q, q, q);
+    }
+    *reinterpret_cast<float4*>(o.out + (size_t)u * C + c) = r;
+    if (o.out_w && c == 0) o.out_w[u] = W;
+    return;
+  }
+  for (int r = 0; r < kMultiFinElems / 256; ++r) {
+    const int64_t e = base + r * 256 + threadIdx.x;
+    if (e >= n) return;
+    const int64_t slot = e / C;
+    const int c = (int)(e - slot * C);
+    const uint32_t u = J.a.tgt_perm[slot];
+    if (u == 0xffffffffu) continue;
+    const float2 w2 = J.a.acc_w[slot];
+    const float W = w2.x + w2.y;
+    const float v = (W > 0.f) ? J.a.acc_num[e] / W : __int_as_float(0x7fc00000);
+    if (o.channel_major) o.out[(size_t)c * o.P + u] = v;
+    else o.out[(size_t)u * C + c] = v;
+    if (o.out_w && c == 0) o.out_w[u] = W;
+  }
+}
+
+template <int PB, int CB, int NCG, int MINB>
+cudaError_t launch_multi(const MultiLaunch& L, int nsm, cudaStream_t s) {
+  constexpr int NTH = (kTile / PB) * NCG;
+  auto k = k_grid_f32_multi<PB, CB, NCG, MINB>;
+  const size_t smem = sizeof(F32Smem<PB, CB, NCG>);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTH, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ctas = std::min<int64_t>((int64_t)std::max(1, per_sm) * nsm, L.m.n_items);
+  k<<<(unsigned)ctas, NTH, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int f32_multi_shape(int C) { return f32_default_config(C); }
+
+int f32_multi_cpad(int shape) {
+  static const int cp[kF32MultiShapes] = {4, 8, 16, 32, 64, 128, 256};
+  return cp[shape < 0 ? 0 : (shape >= kF32MultiShapes ? kF32MultiShapes - 1 : shape)];
+}
+
+cudaError_t grid_f32_multi(const F32Multi& m, cudaStream_t s, int64_t* launches) {
+  if (m.n_items <= 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (m.n_jobs > kF32MultiMaxJobs || !m.hjobs) return cudaErrorInvalidValue;
+  static thread_local MultiLaunch L;   // large: not on the stack (the launch copies it)
+  L.m = m;
+  for (int j = 0; j < m.n_jobs; ++j) L.ga[j] = m.hjobs[j].a;
+  k_multi_order<<<1, kOrderCta, 0, s>>>(m);
+  cudaError_t e;
+  switch (m.shape) {
+    case 0: e = launch_multi<1, 4, 1, 12>(L, nsm, s); break;
+    case 1: e = launch_multi<1, 8, 1, 12>(L, nsm, s); break;
+    case 2: e = launch_multi<1, 8, 2, 6>(L, nsm, s); break;
+    case 3: e = launch_multi<2, 8, 4, 5>(L, nsm, s); break;
+    case 4: e = launch_multi<2, 16, 4, 4>(L, nsm, s); break;
+    case 5: e = launch_multi<4, 16, 8, 3>(L, nsm, s); break;
+    default: e = launch_multi<4, 16, 16, 2>(L, nsm, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  int64_t n = 2;   // order, gridder
+  if (m.n_red_blk > 0) {
+    k_multi_reduce<<<(unsigned)m.n_red_blk, kMultiRedElems, 0, s>>>(m);
+    ++n;
+  }
+  k_multi_fixup<<<(unsigned)nsm, kFixThreads, 0, s>>>(m);
+  if (m.n_fin_blk > 0) {
+    // only jobs whose maps the gridder did not write (splits, channel-major)
+    k_multi_finalize<<<(unsigned)m.n_fin_blk, 256, 0, s>>>(m);
+    ++n;
+  }
+  if (launches) *launches += n + 1;
   return cudaGetLastError();
 }
 

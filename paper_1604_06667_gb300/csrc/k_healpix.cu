@@ -270,6 +270,216 @@ __global__ void k_export_ring(const int32_t* __restrict__ ro, int64_t m, int64_t
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Fused batches: the sample index of all jobs at once.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Largest j with off[j] <= x (off[0] = 0, x < off[n]).
+__device__ __forceinline__ int batch_job(const int64_t* __restrict__ off, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// k_sample_keys for every job: composite key (job key base + RING key at the
+// job's nside), the sample's index within its job, its unit vector record
+// and FP64 lon/lat at its batch position.  CTA b serves 256 samples of the
+// job whose CTA range (blk: prefix of the jobs' CTA counts) holds b.
+__global__ void __launch_bounds__(256) k_batch_keys(const BatchIndexJob* __restrict__ jobs,
+                                                    const int64_t* __restrict__ blk, int n_jobs,
+                                                    uint64_t* __restrict__ key,
+                                                    uint32_t* __restrict__ val,
+                                                    float4* __restrict__ u_hi,
+                                                    float4* __restrict__ u_lo,
+                                                    double2* __restrict__ sll, unsigned* err) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = batch_job(blk, n_jobs, blockIdx.x);
+  __syncthreads();
+  const int j = s_job;
+  const BatchIndexJob& J = jobs[j];
+  const int64_t li = (int64_t)(blockIdx.x - blk[j]) * 256 + threadIdx.x;
+  if (li >= J.n) return;
+  const int64_t i = J.off + li;
+  const int64_t ns = J.nside;
+  const double lo = J.lon[li], la = J.lat[li];
+  val[i] = (uint32_t)li;
+  sll[i] = make_double2(lo, la);
+  if (!valid_coord(lo, la)) {
+    key[i] = J.key_base + (uint64_t)(12 * ns * ns);
+    u_hi[i] = make_float4(4.f, 4.f, 4.f, 0.f);
+    u_lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    set_error(err, ERR_BAD_SAMPLE);
+    return;
+  }
+  df32 sb, cb, sl, cl;
+  key[i] = J.key_base + (uint64_t)key_and_sincos(ns, lo, la, sb, cb, sl, cl);
+  const df32 x = df_mul(cb, cl), y = df_mul(cb, sl);
+  float w = 1.f;
+  if (J.weights) {
+    w = J.weights[li];
+    if (!(w >= 0.f) || !isfinite(w)) {
+      set_error(err, ERR_BAD_SAMPLE);
+      w = 0.f;
+    }
+  }
+  u_hi[i] = make_float4(x.hi, y.hi, sb.hi, w);
+  u_lo[i] = make_float4(x.lo, y.lo, sb.lo, 0.f);
+}
+
+// k_sample_gather for every job: each thread covers one position s = 0 .. n
+// of its job's segment (CTA b serves 256 of them, blk: prefix of the jobs'
+// CTA counts for n + 1 positions); ring offsets are relative to the segment,
+// so that each job sees its own index as if it ran alone.
+__global__ void __launch_bounds__(256) k_batch_gather(const BatchIndexJob* __restrict__ jobs,
+                                                      const int64_t* __restrict__ blk, int n_jobs,
+                                                      const uint64_t* __restrict__ skey64,
+                                                      const uint32_t* __restrict__ sval,
+                                                      const float4* __restrict__ u_hi,
+                                                      const float4* __restrict__ u_lo,
+                                                      float4* __restrict__ s_hi,
+                                                      float4* __restrict__ s_lo,
+                                                      uint32_t* __restrict__ skey,
+                                                      int32_t* __restrict__ ring_off) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = batch_job(blk, n_jobs, blockIdx.x);
+  __syncthreads();
+  const int j = s_job;
+  const BatchIndexJob& J = jobs[j];
+  const int64_t s = (int64_t)(blockIdx.x - blk[j]) * 256 + threadIdx.x;   // 0 .. n
+  if (s > J.n) return;
+  const int64_t ns = J.nside;
+  const int64_t npix = 12 * ns * ns;
+  const int64_t end = 4 * ns;
+  int64_t rc = end;
+  if (s < J.n) {
+    const int64_t gs = J.off + s;
+    const uint32_t idx = sval[gs];
+    s_hi[gs] = u_hi[J.off + idx];
+    s_lo[gs] = u_lo[J.off + idx];
+    const int64_t k = (int64_t)(skey64[gs] - J.key_base);
+    skey[gs] = (uint32_t)k;
+    rc = (k >= npix) ? end : ring_of_key(ns, J.lg, k);
+  }
+  int64_t rp = -1;
+  if (s > 0) {
+    const int64_t k = (int64_t)(skey64[J.off + s - 1] - J.key_base);
+    rp = (k >= npix) ? end : ring_of_key(ns, J.lg, k);
+  }
+  int32_t* ro = ring_off + J.ring_base;
+  for (int64_t i = rp + 1; i <= rc; ++i) ro[i] = (int32_t)s;
+}
+
+// k_tile_ranges for the tiles of every job (one warp per tile).
+__global__ void k_batch_ranges(const BatchIndexJob* __restrict__ jobs,
+                               const int64_t* __restrict__ tile_off, int n_jobs, int64_t n_tiles,
+                               const int32_t* __restrict__ ring_off_all,
+                               const uint32_t* __restrict__ skey_all) {
+  const int64_t gt = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gt >= n_tiles) return;
+  const int j = batch_job(tile_off, n_jobs, gt);
+  const BatchIndexJob& J = jobs[j];
+  const int64_t tile = gt - tile_off[j];
+  const int32_t* ring_off = ring_off_all + J.ring_base;
+  const uint32_t* skey = skey_all + J.off;
+  const int64_t r0 = J.range_off[tile], r1 = J.range_off[tile + 1];
+  int32_t running = 0;
+  for (int64_t b = r0; b < r1; b += 32) {
+    const int64_t r = b + lane;
+    int32_t lo = 0, hi = 0;
+    if (r < r1) {
+      const Range q = J.ranges[r];
+      const int32_t a = ring_off[q.ring], e = ring_off[q.ring + 1];
+      lo = a;
+      hi = a;
+      if (e > a) {
+        lo = lower_bound_u32(skey, a, e, (uint32_t)q.pix_lo);
+        hi = lower_bound_u32(skey, lo, e, (uint32_t)q.pix_hi + 1u);
+      }
+    }
+    const int32_t cnt = hi - lo;
+    int32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (r < r1) {
+      J.range_s[r] = make_int2(lo, hi);
+      J.range_c[r] = running + incl - cnt;
+    }
+    running += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) J.tile_cand[tile] = running;
+}
+
+}  // namespace
+
+cudaError_t batch_index_alloc(BatchIndex& bi, cudaStream_t s) {
+  const size_t n = (size_t)bi.N;
+  cudaError_t e;
+  if ((e = dalloc(&bi.key, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.val, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.u_hi, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.u_lo, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.sll, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.s_hi, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.s_lo, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.skey, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.ring_off, (size_t)bi.n_ring, s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+void batch_index_free(BatchIndex& bi, cudaStream_t s) {
+  dfree(bi.jobs, s);
+  dfree(bi.key_blk, s);
+  dfree(bi.gth_blk, s);
+  dfree(bi.tile_off, s);
+  dfree(bi.key, s);
+  dfree(bi.val, s);
+  dfree(bi.u_hi, s);
+  dfree(bi.u_lo, s);
+  dfree(bi.sll, s);
+  dfree(bi.s_hi, s);
+  dfree(bi.s_lo, s);
+  dfree(bi.skey, s);
+  dfree(bi.ring_off, s);
+  if (bi.sw.keys_alt) cudaFreeAsync(bi.sw.keys_alt, s);
+  bi.sw.keys_alt = nullptr;
+  dfree(bi.sw.vals_alt, s);
+  dfree(bi.sw.hist, s);
+  dfree(bi.sw.totals, s);
+  dfree(bi.sw.status, s);
+  dfree(bi.sw.os_meta, s);
+  bi.sw = SortWork();
+  bi.sorted_key = nullptr;
+  bi.sorted_val = nullptr;
+}
+
+cudaError_t batch_index_run(BatchIndex& bi, unsigned* err, cudaStream_t s, int64_t* launches) {
+  if (bi.N <= 0) return cudaSuccess;
+  k_batch_keys<<<(unsigned)bi.n_key_blk, 256, 0, s>>>(bi.jobs, bi.key_blk, bi.n_jobs, bi.key,
+                                                      bi.val, bi.u_hi, bi.u_lo, bi.sll, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = radix_sort_u64(bi.key, bi.val, bi.N, bi.key_bits, bi.sw, s, &bi.sorted_key, &bi.sorted_val);
+  if (e != cudaSuccess) return e;
+  k_batch_gather<<<(unsigned)bi.n_gth_blk, 256, 0, s>>>(
+      bi.jobs, bi.gth_blk, bi.n_jobs, bi.sorted_key, bi.sorted_val, bi.u_hi, bi.u_lo, bi.s_hi,
+      bi.s_lo, bi.skey, bi.ring_off);
+  if (bi.n_tiles > 0) {
+    const int warps = 8;
+    k_batch_ranges<<<ceil_div(bi.n_tiles, warps), 32 * warps, 0, s>>>(
+        bi.jobs, bi.tile_off, bi.n_jobs, bi.n_tiles, bi.ring_off, bi.skey);
+  }
+  if (launches) *launches += 3 + 3 * ((bi.key_bits + 7) / 8);
+  return cudaGetLastError();
+}
+
 int key_bits_for(int64_t ns) {
   const uint64_t maxkey = (uint64_t)(12 * ns * ns);  // sentinel for invalid samples
   int b = 0;

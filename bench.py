@@ -498,8 +498,8 @@ def time_differentiable(args, dev):
 # ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (summary under
 # profiles/); valid only for the kernel source it was taken with.
 TRAFFIC_CAPTURE = {"source": "paper_1604_06667_gb300/csrc/k_grid_tc.cu",
-                   "sha256": "6d288cefe4dc1a2510d3a314a90da626f2b58194352a8f6ca61e3f0976f38380",
-                   "bytes_per_launch": 2238623488 + 260987904}
+                   "sha256": "09a12d2114b08ca2812bfb672a5a3c7f22ae888c33bf1297b2ecbec0d2f60856",
+                   "bytes_per_launch": 936303872 + 262425600}
 
 
 def captured_traffic():

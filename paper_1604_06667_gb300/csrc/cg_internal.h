@@ -55,7 +55,7 @@ struct Tiling {           // geometry of one tiling of the targets
   int2* range_s = nullptr;        // [n_ranges] sample ranges [lo, hi) of the last add
   int32_t* range_c = nullptr;     // [n_ranges] the tile's candidates before each range
   int32_t* tile_cand = nullptr;   // [n_tiles] candidates per tile of the last add
-  int32_t* order = nullptr;       // [cap_order] persistent-kernel items by decreasing cost
+  int32_t* order = nullptr;       // [cap_order] persistent schedule: waves of neighbouring items
   int64_t cap_order = 0;
   // 128-target tiles only: the four 32-target quarters (one TMEM lane quarter
   // each; k-d leaves), FP64 centre + radius, and the centre relative to the

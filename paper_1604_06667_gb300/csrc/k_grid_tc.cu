@@ -197,18 +197,16 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo,
   return smem_desc(addr, lbo, sbo) | ((uint64_t)2 << 61);  // layout: 128-byte swizzle
 }
 
-// Item k of this CTA's sequence, -1 past its end.  With an order (items
-// ranked by decreasing cost), round k deals ranks k G .. k G + G - 1 to the G
-// CTAs, forwards on even rounds and backwards on odd ones, so every CTA gets
-// a similar total; without one, CTA b takes items b, b + G, b + 2 G, ...
+// Item k of this CTA's sequence, -1 past its end.  With an order (round k
+// of the schedule is a wave of G spatially consecutive items, dealt to the G
+// CTAs by k_item_waves), CTA b takes order[k G + b]; without one, items b,
+// b + G, b + 2 G, ...
 __device__ __forceinline__ int64_t item_at(const TcArgs& a, int64_t n_items, int64_t k) {
   const int64_t G = gridDim.x;
-  if (!a.order) {
-    const int64_t it = (int64_t)blockIdx.x + k * G;
-    return it < n_items ? it : -1;
-  }
-  const int64_t pos = k * G + ((k & 1) ? G - 1 - (int64_t)blockIdx.x : (int64_t)blockIdx.x);
-  return pos < n_items ? (int64_t)a.order[pos] : -1;
+  const int64_t pos = (int64_t)blockIdx.x + k * G;
+  if (!a.order) return pos < n_items ? pos : -1;
+  const int64_t waves = (n_items + G - 1) / G;
+  return pos < waves * G ? (int64_t)a.order[pos] : -1;
 }
 
 __device__ __forceinline__ int chunks_of(const TcArgs& a, int64_t item) {
@@ -970,66 +968,62 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   }
 }
 
-// Items ranked by decreasing cost for the persistent schedule (item_at):
-// cost = the tile's chunks + 8 (the epilogue's share of an item), clamped to
-// kOrderBins - 1; one CTA counting-sorts the items on it.  Items of equal cost
-// take their ranks in any order (the assignment does not change any result:
-// every item is computed whole by one CTA).
-constexpr int kOrderBins = 4096;
-constexpr int kOrderThreads = 1024;
+// The persistent schedule (item_at): items in tile order -- the k-d order of
+// the targets, so consecutive items are neighbours on the sky -- cut into
+// waves of G, one item per CTA.  Inside a wave the items are ranked by cost
+// (the tile's chunks + 8, the epilogue's share of an item) and the ranks
+// dealt to the CTAs forwards on even waves and backwards on odd ones, so
+// that the CTAs' totals stay close while the items running at any time stay
+// within a wave or two: a compact patch of sky whose candidate rows the
+// 129 MB L2 can hold, instead of a cost-ranked scatter of tiles that each
+// read their halo from DRAM.  One CTA per wave; a bitonic sort of the wave's
+// (cost, item) keys; CTAs left without an item in the last wave get -1.
+// The assignment changes no result (every item is computed whole by one CTA).
+constexpr int kWaveThreads = 512;
+constexpr int kWaveMax = 1024;   // G <= kWaveMax
 
-__device__ __forceinline__ int order_bin(int32_t cand) {
-  const int c = (cand + kK - 1) / kK + 8;
-  return kOrderBins - 1 - min(c, kOrderBins - 1);
-}
-
-__global__ void __launch_bounds__(kOrderThreads) k_item_order(const int32_t* __restrict__ tile_cand,
-                                                              int n_slabs, int64_t n_items,
-                                                              int32_t* __restrict__ order) {
-  __shared__ int32_t cnt[kOrderBins];
-  __shared__ int32_t wsum[kOrderThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < kOrderBins; i += kOrderThreads) cnt[i] = 0;
-  __syncthreads();
-  for (int64_t it = tid; it < n_items; it += kOrderThreads)
-    atomicAdd(&cnt[order_bin(tile_cand[it / n_slabs])], 1);
-  __syncthreads();
-  // exclusive scan of the bins: thread t owns bins 4 t .. 4 t + 3
-  constexpr int kPer = kOrderBins / kOrderThreads;
-  int v[kPer], sum = 0;
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    v[j] = cnt[kPer * tid + j];
-    sum += v[j];
-  }
-  int incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int x = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+__global__ void __launch_bounds__(kWaveThreads) k_item_waves(const int32_t* __restrict__ tile_cand,
+                                                             int n_slabs, int64_t n_items, int G,
+                                                             int32_t* __restrict__ order) {
+  __shared__ uint64_t key[kWaveMax];
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * G;
+  const int64_t left = n_items - base;
+  const int n = left < (int64_t)G ? (int)left : G;
+  int P = 1;
+  while (P < G) P <<= 1;
+  for (int i = tid; i < P; i += kWaveThreads) {
+    uint64_t k = 0;   // padding sorts last
+    if (i < n) {
+      const int64_t it = base + i;
+      const uint32_t cost = (uint32_t)((tile_cand[it / n_slabs] + kK - 1) / kK + 8);
+      // descending cost, then ascending item (the key holds ~item)
+      k = ((uint64_t)cost << 32) | (uint64_t)(0xffffffffu - (uint32_t)it);
     }
-    wsum[lane] = x;
+    key[i] = k;
   }
   __syncthreads();
-  int base = incl - sum + (warp > 0 ? wsum[warp - 1] : 0);
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    cnt[kPer * tid + j] = base;
-    base += v[j];
+  // bitonic sort, descending
+  for (int kk = 2; kk <= P; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < P; i += kWaveThreads) {
+        const int l = i ^ jj;
+        if (l > i) {
+          const uint64_t x = key[i], y = key[l];
+          const bool desc = (i & kk) == 0;
+          if (desc ? (x < y) : (x > y)) {
+            key[i] = y;
+            key[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  for (int64_t it = tid; it < n_items; it += kOrderThreads) {
-    const int pos = atomicAdd(&cnt[order_bin(tile_cand[it / n_slabs])], 1);
-    order[pos] = (int32_t)it;
+  for (int r = tid; r < G; r += kWaveThreads) {
+    const int cta = (blockIdx.x & 1) ? G - 1 - r : r;
+    order[base + cta] =
+        r < n ? (int32_t)(0xffffffffu - (uint32_t)(key[r] & 0xffffffffu)) : -1;
   }
 }
 
@@ -1143,19 +1137,21 @@ cudaError_t grid_tiles_tc(cg_grid* g, const void* data, int mode, float* out, fl
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) return cudaSuccess;
-  // balanced persistent schedule: with several items per CTA, rank the items
-  // by cost so that the CTAs' totals match (tiles differ in candidates)
+  // balanced persistent schedule with several items per CTA: waves of
+  // neighbouring items, ranked by cost inside each wave (k_item_waves)
   a.order = nullptr;
-  if (items > grid && items <= INT32_MAX) {
+  if (items > grid && items <= INT32_MAX && grid <= kWaveMax) {
     Tiling& tw = g->t128;
-    if (tw.cap_order < items) {
+    const int64_t waves = (items + grid - 1) / grid;
+    if (tw.cap_order < waves * grid) {
       dfree(tw.order, g->stream);
       tw.cap_order = 0;
-      cudaError_t ea = dalloc(&tw.order, (size_t)items, g->stream);
+      cudaError_t ea = dalloc(&tw.order, (size_t)(waves * grid), g->stream);
       if (ea != cudaSuccess) return ea;
-      tw.cap_order = items;
+      tw.cap_order = waves * grid;
     }
-    k_item_order<<<1, kOrderThreads, 0, g->stream>>>(t.tile_cand, a.n_slabs, items, tw.order);
+    k_item_waves<<<(unsigned)waves, kWaveThreads, 0, g->stream>>>(t.tile_cand, a.n_slabs, items,
+                                                                  (int)grid, tw.order);
     g->n_launches += 1;
     a.order = tw.order;
   }

@@ -498,8 +498,8 @@ def time_differentiable(args, dev):
 # ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (summary under
 # profiles/); valid only for the kernel source it was taken with.
 TRAFFIC_CAPTURE = {"source": "paper_1604_06667_gb300/csrc/k_grid_tc.cu",
-                   "sha256": "09a12d2114b08ca2812bfb672a5a3c7f22ae888c33bf1297b2ecbec0d2f60856",
-                   "bytes_per_launch": 936303872 + 262425600}
+                   "sha256": "3e561e8b1826564df4792670765e39acc7f8e740c023143b66a485656258c3d7",
+                   "bytes_per_launch": 961199616 + 263374592}
 
 
 def captured_traffic():

@@ -646,14 +646,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       }
       const float invW = (W > 0.f) ? 1.f / W : __int_as_float(0x7fc00000);
       // A non-finite channel value of one candidate reaches every row of the
-      // MMA (0 x NaN): a row whose numerator is not finite is flagged and
-      // computed again by the fix-up pass (paper Eq. 1-2: only the pairs
-      // inside the support take part).  A sum of the row's values turns
-      // non-finite when one of them is (or, harmlessly, on an overflow, which
-      // only sends the row to the exact fix-up).  Accumulating calls look
-      // first and leave the row untouched; one-shot calls write it and let
-      // the fix-up overwrite it.
+      // MMA (0 x NaN, w x Inf): its column is non-finite in all 128 rows.
+      // Flagged rows are computed again by the fix-up pass (paper Eq. 1-2:
+      // only the pairs inside the support take part).  A sum of a row's
+      // values turns non-finite when one of them is (or, harmlessly, on an
+      // overflow, which only sends the row to the exact fix-up).
+      // Accumulating calls check every row first and leave flagged rows
+      // untouched; one-shot calls write the rows, and the first epilogue
+      // warp's rows stand for the whole tile (every row of a contaminated
+      // tile is flagged, the fix-up overwrites them).
       float2 fin2 = make_float2(0.f, 0.f);
+      const bool chk_tile = a.mode == 2 && nch && warp == kEpiWarp;
       if (a.mode != 2 && nch) {
         for (int cb = 0; cb < cp; cb += 16) {
           uint32_t r[16];
@@ -696,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(tmem_d + lane_off + (uint32_t)(cb + 16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (a.mode == 2 && nch) {
+        if (chk_tile) {
 #pragma unroll
           for (int j = 0; j < 32; j += 2)
             fin2 = __fadd2_rn(fin2, make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])));
@@ -741,7 +744,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         __syncwarp();
       }
-      if (valid && nch && !isfinite(fin2.x + fin2.y)) {
+      if (chk_tile) {
+        if (__any_sync(0xffffffffu, !isfinite(fin2.x + fin2.y))) {
+#pragma unroll
+          for (int q2 = 0; q2 < kT / 32; ++q2) {
+            const uint64_t e = (uint64_t)(tile * kT + 32 * q2 + lane) * (uint64_t)a.n_slabs + (uint64_t)slab;
+            atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
+          }
+          if (lane == 0) atomicOr(a.nf_any, 1u);
+        }
+      } else if (a.mode != 2 && valid && nch && !isfinite(fin2.x + fin2.y)) {
         const uint64_t e = (uint64_t)slot * (uint64_t)a.n_slabs + (uint64_t)slab;
         atomicOr(&a.nf_bits[e >> 5], 1u << (e & 31));
         atomicOr(a.nf_any, 1u);

@@ -14,7 +14,8 @@
 //            tile-relative FP32 vectors, exact cut d <= r (FP64 recomputation
 //            inside a narrow guard band around r), Gaussian via ex2;
 //            per-target weight sums W_p with Neumaier compensation;
-//   phase B  register-blocked accumulation acc[p][c] += w[k][p] * D[k][c],
+//   phase B  register-blocked accumulation acc[p][c] += w[k][p] * D[k][c]
+//            (packed f32x2 FMAs on channel pairs),
 //            skipping candidates whose weights for the thread's targets are 0.
 // The epilogue adds acc into the numerator and W into the weight map (tile
 // order; cg_grid_finalize applies Eq. 3 and the user layout).  A target row
@@ -177,11 +178,13 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
   // phase-B identity
   const int pg = tid / NCG;
   const int cg = tid % NCG;
-  float acc[PB][CB];
+  // channel sums as packed pairs (channels 2 m, 2 m + 1 of the thread's
+  // blocks): one fma.rn.f32x2 does both, the same IEEE fma per lane
+  float2 acc[PB][CB / 2];
 #pragma unroll
   for (int i = 0; i < PB; ++i)
 #pragma unroll
-    for (int j = 0; j < CB; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < CB / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   const DT* data = static_cast<const DT*>(a.data);
   const int C = a.C;
@@ -373,15 +376,17 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
 #pragma unroll
         for (int i = 0; i < PB; ++i) any |= (wv[i] != 0.f);
         if (!any) continue;
+        float2 w2[PB];
+#pragma unroll
+        for (int i = 0; i < PB; ++i) w2[i] = make_float2(wv[i], wv[i]);
 #pragma unroll
         for (int q4 = 0; q4 < CB / 4; ++q4) {
           const float4 dv = *reinterpret_cast<const float4*>(&S.d[cur][k][4 * cg + 4 * NCG * q4]);
+          const float2 d01 = make_float2(dv.x, dv.y), d23 = make_float2(dv.z, dv.w);
 #pragma unroll
           for (int i = 0; i < PB; ++i) {
-            acc[i][4 * q4 + 0] = fmaf(wv[i], dv.x, acc[i][4 * q4 + 0]);
-            acc[i][4 * q4 + 1] = fmaf(wv[i], dv.y, acc[i][4 * q4 + 1]);
-            acc[i][4 * q4 + 2] = fmaf(wv[i], dv.z, acc[i][4 * q4 + 2]);
-            acc[i][4 * q4 + 3] = fmaf(wv[i], dv.w, acc[i][4 * q4 + 3]);
+            acc[i][2 * q4] = __ffma2_rn(w2[i], d01, acc[i][2 * q4]);
+            acc[i][2 * q4 + 1] = __ffma2_rn(w2[i], d23, acc[i][2 * q4 + 1]);
           }
         }
       }
@@ -404,7 +409,7 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
     for (int i = 0; i < PB; ++i) {
       chk[i] = 0.f;
 #pragma unroll
-      for (int j = 0; j < CB; ++j) chk[i] += acc[i][j];
+      for (int j = 0; j < CB / 2; ++j) chk[i] += acc[i][j].x + acc[i][j].y;
     }
     const unsigned any_bad = __syncthreads_or([&] {
       bool b = false;
@@ -471,7 +476,9 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c = c_base + 4 * cg + 4 * NCG * q + j;
-          if (c < C) dst[c] = (W > 0.f) ? acc[i][4 * q + j] / W : __int_as_float(0x7fc00000);
+          const float2 v2 = acc[i][2 * q + (j >> 1)];
+          const float v = (j & 1) ? v2.y : v2.x;
+          if (c < C) dst[c] = (W > 0.f) ? v / W : __int_as_float(0x7fc00000);
         }
     }
     return;
@@ -491,7 +498,9 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = c_base + 4 * cg + 4 * NCG * q + j;
-        if (c < C) dst[c] = add ? dst[c] + acc[i][4 * q + j] : acc[i][4 * q + j];
+        const float2 v2 = acc[i][2 * q + (j >> 1)];
+        const float v = (j & 1) ? v2.y : v2.x;
+        if (c < C) dst[c] = add ? dst[c] + v : v;
       }
   }
   // ---- epilogue: weight map and pair count (first channel slab only) ----

@@ -320,6 +320,18 @@ cg_status cg_grid_oneshot_pcw(cg_grid* g, const double* lon_deg, const double* l
 cg_status cg_grid_dsigma(cg_grid* g, const void* data, int32_t data_dtype, const float* grad_out,
                          float* dR, double* dsigma);
 
+/* Map making by gradient descent on L(m) = 1/2 ||G^T m - D||^2, G the
+ * normalised gridding operator of Eq. 3 and G^T its adjoint (cg_degrid): the
+ * element-wise steps of an iteration, on the handle's stream.
+ *   cg_md_residual: r <- r - data (device float32 [n], r = G^T m on entry)
+ *                   and *loss <- 1/2 sum r^2 in FP64 (device double; a fixed
+ *                   summation order, so repeated calls agree bit for bit);
+ *   cg_md_update:   m <- m - alpha grad (device float32 [n]), where grad is
+ *                   NaN (a target no sample reaches) it counts as 0.
+ * CG_EINVAL for null pointers, n < 0 or a non-finite alpha. */
+cg_status cg_md_residual(cg_grid* g, float* r, const float* data, int64_t n, double* loss);
+cg_status cg_md_update(cg_grid* g, float* m, const float* grad, float alpha, int64_t n);
+
 /* Copy out the sample index built by the last cg_grid_add (the sorted
  * replacement for the paper's hash tables, Sect. 3.4):
  *   sorted_pix  device [n] int64: RING indices in ascending order;

@@ -88,6 +88,8 @@ SIGNATURES = {
     "cg_batch_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
     "cg_batch_destroy": [_vp],
     "cg_batch_set_fused": [_vp, _i32],
+    "cg_md_residual": [_vp, _vp, _vp, _i64, _vp],
+    "cg_md_update": [_vp, _vp, _vp, ctypes.c_float, _i64],
     "cg_batch_sync": [_vp],
     "cg_batch_debug_hold": [_vp, _i32, _i64],
 }
@@ -162,6 +164,8 @@ cg_batch_get_choice = _call("cg_batch_get_choice")
 cg_batch_info = _call("cg_batch_info")
 cg_batch_destroy = _call("cg_batch_destroy")
 cg_batch_set_fused = _call("cg_batch_set_fused")
+cg_md_residual = _call("cg_md_residual")
+cg_md_update = _call("cg_md_update")
 cg_batch_sync = _call("cg_batch_sync")
 cg_batch_debug_hold = _call("cg_batch_debug_hold")
 

@@ -111,8 +111,7 @@ void free_all(cg_grid* g) {
   dfree(g->sw.os_meta, s);
   dfree(g->s_hi, s);
   dfree(g->s_lo, s);
-  dfree(g->u_hi, s);
-  dfree(g->u_lo, s);
+  dfree(g->u_rec, s);
   dfree(g->s_ll, s);
   dfree(g->ring_off, s);
   dfree(g->tix_key, s);
@@ -149,6 +148,8 @@ void free_all(cg_grid* g) {
   dfree(g->nf_any, s);
   g->nf_words = 0;
   dfree(g->d_hold, s);
+  dfree(g->md_part, s);
+  g->md_cap = 0;
   release_events(g);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
@@ -827,6 +828,28 @@ cg_status cg_grid_export_index(cg_grid* g, int64_t* sorted_pix, int64_t* perm,
   if (n > 0 && (!sorted_pix || !perm)) return fail(CG_EINVAL, "cg_grid_export_index: null pointer");
   CG_CUDA(cudaSetDevice(g->device), "cg_grid_export_index");
   CG_CUDA(export_index(g, sorted_pix, perm, ring_off, n), "cg_grid_export_index");
+  return CG_OK;
+}
+
+cg_status cg_md_residual(cg_grid* g, float* r, const float* data, int64_t n, double* loss) {
+  g_last_error.clear();
+  const char* where = "cg_md_residual";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (n < 0 || (n > 0 && (!r || !data)) || !loss)
+    return fail(CG_EINVAL, "%s: null pointer or negative size", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  CG_CUDA(md_residual(g, r, data, n, loss), where);
+  return CG_OK;
+}
+
+cg_status cg_md_update(cg_grid* g, float* m, const float* grad, float alpha, int64_t n) {
+  g_last_error.clear();
+  const char* where = "cg_md_update";
+  if (!g) return fail(CG_EINVAL, "%s: null handle", where);
+  if (n < 0 || (n > 0 && (!m || !grad))) return fail(CG_EINVAL, "%s: null pointer or negative size", where);
+  if (!std::isfinite(alpha)) return fail(CG_EINVAL, "%s: alpha must be finite", where);
+  CG_CUDA(cudaSetDevice(g->device), where);
+  CG_CUDA(md_update(g, m, grad, alpha, n), where);
   return CG_OK;
 }
 

@@ -141,8 +141,9 @@ struct cg_grid {
   uint32_t* sorted_val = nullptr;
   float4* s_hi = nullptr;         // [cap_n] sorted samples: unit vector hi, w = omega
   float4* s_lo = nullptr;         // [cap_n] unit vector lo
-  float4* u_hi = nullptr;         // [cap_n] input order: unit vector hi, w = omega
-  float4* u_lo = nullptr;         // [cap_n] input order: unit vector lo
+  // [2 cap_n] input order: per sample one 32-byte record, unit vector hi
+  // (w = omega) then lo, so that the gather into sorted order reads one sector
+  float4* u_rec = nullptr;
   double2* s_ll = nullptr;        // [cap_n] input order: FP64 lon/lat (guard-band decisions)
   int32_t* ring_off = nullptr;    // [4*nside + 1]
   int64_t last_n = 0;
@@ -170,6 +171,8 @@ struct cg_grid {
   float* ds_num0 = nullptr;       // [slots][C] (w pass)
   float2* ds_w0 = nullptr;        // [slots]
   double* ds_part = nullptr;      // per-block partial sums
+  double* md_part = nullptr;      // map making: per-block partial sums of r^2
+  size_t md_cap = 0;
   // one weight per sample and channel: [N][2C] (omega D | omega) and its
   // [slots][2C] accumulators (cg_grid_oneshot_pcw)
   float* pcw_data = nullptr;
@@ -240,10 +243,11 @@ cudaError_t unit_vectors(const double* lon, const double* lat, int64_t n, double
 cudaError_t samples_sort(cg_grid* g, int64_t n);
 cudaError_t samples_prepare(cg_grid* g, int64_t n);
 int key_bits_for(int64_t ns);   // bits of a RING key at nside (incl. the invalid sentinel)
-// gather (hi, lo) records into sorted order and build ring offsets [4 ns + 1]
+// gather (hi, lo) records into sorted order and build ring offsets [4 ns + 1];
+// record i is u_hi[i * stride], u_lo[i * stride]
 cudaError_t sorted_gather(int64_t ns, const uint32_t* skey, const uint32_t* sval,
-                          const float4* u_hi, const float4* u_lo, int64_t n, float4* s_hi,
-                          float4* s_lo, int32_t* ring_off, cudaStream_t s);
+                          const float4* u_hi, const float4* u_lo, int stride, int64_t n,
+                          float4* s_hi, float4* s_lo, int32_t* ring_off, cudaStream_t s);
 cudaError_t tiles_ranges(cg_grid* g, Tiling& t);
 cudaError_t tiles_query(cg_grid* g, Tiling& t);
 void tiling_free(Tiling& t, cudaStream_t s);
@@ -342,8 +346,7 @@ struct BatchIndex {
   int64_t* tile_off = nullptr;      // device [n_jobs + 1]: prefix of n_tiles
   uint64_t* key = nullptr;          // [N] composite keys, input order
   uint32_t* val = nullptr;          // [N] the sample's index within its job
-  float4* u_hi = nullptr;           // [N] input order
-  float4* u_lo = nullptr;
+  float4* u_rec = nullptr;          // [2 N] input order: (hi, lo) records
   double2* sll = nullptr;
   float4* s_hi = nullptr;           // [N] sorted order
   float4* s_lo = nullptr;
@@ -447,6 +450,9 @@ cudaError_t grid_degrid(cg_grid* g, const float* y, const float* wmap, float* ou
                         bool interp = false, float* vsum = nullptr);
 cudaError_t grid_dsigma(cg_grid* g, const void* data, int dtype, const float* grad, float* dR,
                         double* dsigma);
+// map making: r <- r - d with *loss = 1/2 sum r^2 (FP64); m <- m - alpha grad
+cudaError_t md_residual(cg_grid* g, float* r, const float* d, int64_t n, double* loss);
+cudaError_t md_update(cg_grid* g, float* m, const float* grad, float alpha, int64_t n);
 
 cudaError_t finalize_maps(cg_grid* g, float* out, int channel_major, float* out_w);
 

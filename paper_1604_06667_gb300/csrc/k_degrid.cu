@@ -377,7 +377,7 @@ cudaError_t target_index_build(cg_grid* g) {
                           &g->tix_sslot)) != cudaSuccess)
     return e;
   g->n_launches += 1 + (bits + 7) / 8;
-  if ((e = sorted_gather(g->nside, g->tix_skey, g->tix_sslot, g->tix_uhi, g->tix_ulo, m,
+  if ((e = sorted_gather(g->nside, g->tix_skey, g->tix_sslot, g->tix_uhi, g->tix_ulo, 1, m,
                          g->tix_hi, g->tix_lo, g->tix_ring_off, s)) != cudaSuccess)
     return e;
   g->n_launches += 1;
@@ -468,6 +468,90 @@ cudaError_t grid_dsigma(cg_grid* g, const void* data, int dtype, const float* gr
     k_dsigma_sum<<<1, kDsBlock, 0, s>>>(g->ds_part, nb, dsigma);
     g->n_launches += 1;
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Map making by gradient descent on 1/2 ||G^T m - D||^2 (G the normalised
+// gridding operator of Eq. 3, G^T its adjoint): the element-wise steps of
+// one iteration, in the library.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kMdBlock = 256;
+constexpr int kMdPer = 4;   // values per thread
+
+// r <- r - D; per-block FP64 partial sums of r^2 (fixed order).
+__global__ void __launch_bounds__(kMdBlock) k_md_residual(float* __restrict__ r,
+                                                          const float* __restrict__ d, int64_t n,
+                                                          double* __restrict__ part) {
+  __shared__ double red[kMdBlock];
+  const int64_t base = (int64_t)blockIdx.x * kMdBlock * kMdPer;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kMdPer; ++k) {
+    const int64_t i = base + (int64_t)k * kMdBlock + threadIdx.x;
+    if (i < n) {
+      const float v = r[i] - d[i];
+      r[i] = v;
+      acc += (double)v * (double)v;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kMdBlock / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// loss = 1/2 sum of the partials (one block, fixed order).
+__global__ void __launch_bounds__(kMdBlock) k_md_loss(const double* __restrict__ part, int64_t nb,
+                                                      double* __restrict__ loss) {
+  __shared__ double red[kMdBlock];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < nb; i += kMdBlock) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kMdBlock / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = 0.5 * red[0];
+}
+
+// m <- m - alpha g, where g is NaN (a target no sample reaches) taking 0.
+__global__ void k_md_update(float* __restrict__ m, const float* __restrict__ g, float alpha,
+                            int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = g[i];
+  if (!isnan(v)) m[i] = fmaf(-alpha, v, m[i]);
+}
+
+}  // namespace
+
+cudaError_t md_residual(cg_grid* g, float* r, const float* d, int64_t n, double* loss) {
+  cudaStream_t s = g->stream;
+  const int64_t nb = (n + kMdBlock * kMdPer - 1) / (kMdBlock * kMdPer);
+  if ((size_t)nb > g->md_cap) {
+    dfree(g->md_part, s);
+    g->md_cap = 0;
+    cudaError_t e = dalloc(&g->md_part, (size_t)(nb > 0 ? nb : 1), s);
+    if (e != cudaSuccess) return e;
+    g->md_cap = (size_t)nb;
+  }
+  if (nb > 0) k_md_residual<<<(unsigned)nb, kMdBlock, 0, s>>>(r, d, n, g->md_part);
+  k_md_loss<<<1, kMdBlock, 0, s>>>(g->md_part, nb, loss);
+  g->n_launches += nb > 0 ? 2 : 1;
+  return cudaGetLastError();
+}
+
+cudaError_t md_update(cg_grid* g, float* m, const float* grad, float alpha, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  k_md_update<<<ceil_div(n, 256), 256, 0, g->stream>>>(m, grad, alpha, n);
+  g->n_launches += 1;
   return cudaGetLastError();
 }
 

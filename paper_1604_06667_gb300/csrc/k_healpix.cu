@@ -144,13 +144,12 @@ __global__ void k_unit_vectors(const double* __restrict__ lon, const double* __r
 
 // Per sample (input order): RING key (invalid samples get npix and sort to
 // the end), identity value for the sort, and the unit vector as (hi, lo)
-// FP32 pairs with w = sample weight.
+// FP32 pairs with w = sample weight, one 32-byte record u[2 i], u[2 i + 1].
 __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
                               const double* __restrict__ lat,
                               const float* __restrict__ weights, int64_t n,
                               uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                              float4* __restrict__ u_hi, float4* __restrict__ u_lo,
-                              double2* __restrict__ sll, unsigned* err) {
+                              float4* __restrict__ u, double2* __restrict__ sll, unsigned* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double lo = lon[i], la = lat[i];
@@ -158,8 +157,8 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
   sll[i] = make_double2(lo, la);
   if (!valid_coord(lo, la)) {
     key[i] = (uint32_t)(12 * ns * ns);
-    u_hi[i] = make_float4(4.f, 4.f, 4.f, 0.f);
-    u_lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    u[2 * i] = make_float4(4.f, 4.f, 4.f, 0.f);
+    u[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     set_error(err, ERR_BAD_SAMPLE);
     return;
   }
@@ -174,8 +173,8 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
       w = 0.f;
     }
   }
-  u_hi[i] = make_float4(x.hi, y.hi, sb.hi, w);
-  u_lo[i] = make_float4(x.lo, y.lo, sb.lo, 0.f);
+  u[2 * i] = make_float4(x.hi, y.hi, sb.hi, w);
+  u[2 * i + 1] = make_float4(x.lo, y.lo, sb.lo, 0.f);
 }
 
 
@@ -185,7 +184,7 @@ __global__ void k_sample_keys(int64_t ns, const double* __restrict__ lon,
 __global__ void k_sample_gather(int64_t ns, int lg, const uint32_t* __restrict__ skey,
                                 const uint32_t* __restrict__ sval,
                                 const float4* __restrict__ u_hi,
-                                const float4* __restrict__ u_lo, int64_t n,
+                                const float4* __restrict__ u_lo, int stride, int64_t n,
                                 float4* __restrict__ s_hi, float4* __restrict__ s_lo,
                                 int32_t* __restrict__ ring_off) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,7 +193,7 @@ __global__ void k_sample_gather(int64_t ns, int lg, const uint32_t* __restrict__
   const int64_t end = 4 * ns;
   int64_t rc = end;
   if (s < n) {
-    const uint32_t idx = sval[s];
+    const int64_t idx = (int64_t)sval[s] * stride;
     s_hi[s] = u_hi[idx];
     s_lo[s] = u_lo[idx];
     const int64_t k = skey[s];
@@ -293,8 +292,7 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchIndexJob* __restr
                                                     const int64_t* __restrict__ blk, int n_jobs,
                                                     uint64_t* __restrict__ key,
                                                     uint32_t* __restrict__ val,
-                                                    float4* __restrict__ u_hi,
-                                                    float4* __restrict__ u_lo,
+                                                    float4* __restrict__ u,
                                                     double2* __restrict__ sll, unsigned* err) {
   __shared__ int s_job;
   if (threadIdx.x == 0) s_job = batch_job(blk, n_jobs, blockIdx.x);
@@ -310,8 +308,8 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchIndexJob* __restr
   sll[i] = make_double2(lo, la);
   if (!valid_coord(lo, la)) {
     key[i] = J.key_base + (uint64_t)(12 * ns * ns);
-    u_hi[i] = make_float4(4.f, 4.f, 4.f, 0.f);
-    u_lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    u[2 * i] = make_float4(4.f, 4.f, 4.f, 0.f);
+    u[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     set_error(err, ERR_BAD_SAMPLE);
     return;
   }
@@ -326,8 +324,8 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchIndexJob* __restr
       w = 0.f;
     }
   }
-  u_hi[i] = make_float4(x.hi, y.hi, sb.hi, w);
-  u_lo[i] = make_float4(x.lo, y.lo, sb.lo, 0.f);
+  u[2 * i] = make_float4(x.hi, y.hi, sb.hi, w);
+  u[2 * i + 1] = make_float4(x.lo, y.lo, sb.lo, 0.f);
 }
 
 // k_sample_gather for every job: each thread covers one position s = 0 .. n
@@ -338,8 +336,7 @@ __global__ void __launch_bounds__(256) k_batch_gather(const BatchIndexJob* __res
                                                       const int64_t* __restrict__ blk, int n_jobs,
                                                       const uint64_t* __restrict__ skey64,
                                                       const uint32_t* __restrict__ sval,
-                                                      const float4* __restrict__ u_hi,
-                                                      const float4* __restrict__ u_lo,
+                                                      const float4* __restrict__ u,
                                                       float4* __restrict__ s_hi,
                                                       float4* __restrict__ s_lo,
                                                       uint32_t* __restrict__ skey,
@@ -357,9 +354,9 @@ __global__ void __launch_bounds__(256) k_batch_gather(const BatchIndexJob* __res
   int64_t rc = end;
   if (s < J.n) {
     const int64_t gs = J.off + s;
-    const uint32_t idx = sval[gs];
-    s_hi[gs] = u_hi[J.off + idx];
-    s_lo[gs] = u_lo[J.off + idx];
+    const int64_t rec = 2 * (J.off + (int64_t)sval[gs]);
+    s_hi[gs] = u[rec];
+    s_lo[gs] = u[rec + 1];
     const int64_t k = (int64_t)(skey64[gs] - J.key_base);
     skey[gs] = (uint32_t)k;
     rc = (k >= npix) ? end : ring_of_key(ns, J.lg, k);
@@ -424,8 +421,7 @@ cudaError_t batch_index_alloc(BatchIndex& bi, cudaStream_t s) {
   cudaError_t e;
   if ((e = dalloc(&bi.key, n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&bi.val, n, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&bi.u_hi, n, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&bi.u_lo, n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&bi.u_rec, 2 * n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&bi.sll, n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&bi.s_hi, n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&bi.s_lo, n, s)) != cudaSuccess) return e;
@@ -441,8 +437,7 @@ void batch_index_free(BatchIndex& bi, cudaStream_t s) {
   dfree(bi.tile_off, s);
   dfree(bi.key, s);
   dfree(bi.val, s);
-  dfree(bi.u_hi, s);
-  dfree(bi.u_lo, s);
+  dfree(bi.u_rec, s);
   dfree(bi.sll, s);
   dfree(bi.s_hi, s);
   dfree(bi.s_lo, s);
@@ -463,13 +458,13 @@ void batch_index_free(BatchIndex& bi, cudaStream_t s) {
 cudaError_t batch_index_run(BatchIndex& bi, unsigned* err, cudaStream_t s, int64_t* launches) {
   if (bi.N <= 0) return cudaSuccess;
   k_batch_keys<<<(unsigned)bi.n_key_blk, 256, 0, s>>>(bi.jobs, bi.key_blk, bi.n_jobs, bi.key,
-                                                      bi.val, bi.u_hi, bi.u_lo, bi.sll, err);
+                                                      bi.val, bi.u_rec, bi.sll, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = radix_sort_u64(bi.key, bi.val, bi.N, bi.key_bits, bi.sw, s, &bi.sorted_key, &bi.sorted_val);
   if (e != cudaSuccess) return e;
   k_batch_gather<<<(unsigned)bi.n_gth_blk, 256, 0, s>>>(
-      bi.jobs, bi.gth_blk, bi.n_jobs, bi.sorted_key, bi.sorted_val, bi.u_hi, bi.u_lo, bi.s_hi,
+      bi.jobs, bi.gth_blk, bi.n_jobs, bi.sorted_key, bi.sorted_val, bi.u_rec, bi.s_hi,
       bi.s_lo, bi.skey, bi.ring_off);
   if (bi.n_tiles > 0) {
     const int warps = 8;
@@ -567,8 +562,7 @@ static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
   dfree(g->val, s);
   dfree(g->s_hi, s);
   dfree(g->s_lo, s);
-  dfree(g->u_hi, s);
-  dfree(g->u_lo, s);
+  dfree(g->u_rec, s);
   dfree(g->s_ll, s);
   g->cap_n = 0;
   cudaError_t e;
@@ -576,8 +570,7 @@ static cudaError_t ensure_samples(cg_grid* g, int64_t n) {
   if ((e = dalloc(&g->val, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->s_hi, (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->s_lo, (size_t)n, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->u_hi, (size_t)n, s)) != cudaSuccess) return e;
-  if ((e = dalloc(&g->u_lo, (size_t)n, s)) != cudaSuccess) return e;
+  if ((e = dalloc(&g->u_rec, 2 * (size_t)n, s)) != cudaSuccess) return e;
   if ((e = dalloc(&g->s_ll, (size_t)n, s)) != cudaSuccess) return e;
   g->cap_n = (size_t)n;
   return cudaSuccess;
@@ -588,7 +581,7 @@ cudaError_t samples_keys(cg_grid* g, const double* lon, const double* lat, const
   cudaError_t e = ensure_samples(g, n);
   if (e != cudaSuccess) return e;
   k_sample_keys<<<ceil_div(n, 256), 256, 0, g->stream>>>(g->nside, lon, lat, weights, n, g->key,
-                                                         g->val, g->u_hi, g->u_lo, g->s_ll,
+                                                         g->val, g->u_rec, g->s_ll,
                                                          g->d_err);
   g->n_launches += 1;
   return cudaGetLastError();
@@ -603,13 +596,13 @@ cudaError_t samples_sort(cg_grid* g, int64_t n) {
 }
 
 cudaError_t sorted_gather(int64_t ns, const uint32_t* skey, const uint32_t* sval,
-                          const float4* u_hi, const float4* u_lo, int64_t n, float4* s_hi,
-                          float4* s_lo, int32_t* ring_off, cudaStream_t s) {
+                          const float4* u_hi, const float4* u_lo, int stride, int64_t n,
+                          float4* s_hi, float4* s_lo, int32_t* ring_off, cudaStream_t s) {
   int lg = -1;
   if ((ns & (ns - 1)) == 0)
     for (lg = 0; ((int64_t)1 << lg) < ns; ++lg) {
     }
-  k_sample_gather<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, lg, skey, sval, u_hi, u_lo, n, s_hi,
+  k_sample_gather<<<ceil_div(n + 1, 256), 256, 0, s>>>(ns, lg, skey, sval, u_hi, u_lo, stride, n, s_hi,
                                                        s_lo, ring_off);
   return cudaGetLastError();
 }
@@ -617,7 +610,7 @@ cudaError_t sorted_gather(int64_t ns, const uint32_t* skey, const uint32_t* sval
 cudaError_t samples_prepare(cg_grid* g, int64_t n) {
   cudaStream_t s = g->stream;
   const int64_t ns = g->nside;
-  cudaError_t e = sorted_gather(ns, g->sorted_key, g->sorted_val, g->u_hi, g->u_lo, n, g->s_hi,
+  cudaError_t e = sorted_gather(ns, g->sorted_key, g->sorted_val, g->u_rec, g->u_rec + 1, 2, n, g->s_hi,
                                 g->s_lo, g->ring_off, s);
   if (e != cudaSuccess) return e;
   g->n_launches += 1;

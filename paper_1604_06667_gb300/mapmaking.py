@@ -12,6 +12,8 @@ from __future__ import annotations
 
 import torch
 
+from . import _capi as C
+
 
 def gd(gridder, lon, lat, data, steps: int = 50, alpha: float | None = None):
     """Returns (m [P, C], losses [steps + 1] float64 on the host, alpha)."""
@@ -26,12 +28,13 @@ def gd(gridder, lon, lat, data, steps: int = 50, alpha: float | None = None):
         alpha = 1.0 / float(colsum.max())
     m = torch.zeros((P, Cc), device=dev, dtype=torch.float32)
     losses = torch.empty(steps + 1, device=dev, dtype=torch.float64)
+    h = gridder._h
     for k in range(steps + 1):
-        r = gridder.degrid(m, map_weights=W)
-        r -= D
-        losses[k] = 0.5 * torch.sum(r.double() * r.double())
+        r = gridder.degrid(m, map_weights=W)                     # G^T m
+        # r <- G^T m - D and the loss 1/2 |r|^2 (FP64), in the library
+        C.cg_md_residual(h, r.data_ptr(), D.data_ptr(), r.numel(), losses[k:].data_ptr())
         if k == steps:
             break
         gridder.grid_oneshot(None, None, r, out=g)               # G r, same samples
-        m -= alpha * torch.nan_to_num(g, nan=0.0)
+        C.cg_md_update(h, m.data_ptr(), g.data_ptr(), float(alpha), m.numel())
     return m, losses.cpu().numpy(), alpha

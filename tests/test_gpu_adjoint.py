@@ -197,3 +197,53 @@ def test_mapmaking_loop_matches_oracle():
     assert np.allclose(losses, lref, rtol=1e-4, atol=0), np.max(np.abs(losses / lref - 1))
     mm = m.double().cpu().numpy()
     assert np.max(np.abs(mm - mref)) <= 1e-4 * np.max(np.abs(mref))
+
+
+def test_mapmaking_steps_in_library():
+    """cg_md_residual / cg_md_update: r <- r - D with 1/2 |r|^2 in FP64 (fixed
+    order: repeated calls agree bit for bit), m <- m - alpha g with NaN g as 0,
+    against numpy in FP64; argument errors."""
+    import ctypes
+    import torch
+    from paper_1604_06667_gb300 import Gridder, _capi
+    rng = np.random.Generator(np.random.PCG64(4242))
+    g = Gridder(np.array([1.0, 2.0]), np.array([0.0, 0.5]), n_channels=1)
+    n = 300_001                      # several blocks and a ragged tail
+    r0 = rng.standard_normal(n).astype(np.float32)
+    d = rng.standard_normal(n).astype(np.float32)
+    r = torch.from_numpy(r0).cuda()
+    dd = torch.from_numpy(d).cuda()
+    loss = torch.zeros(2, dtype=torch.float64, device="cuda")
+    _capi.cg_md_residual(g._h, r.data_ptr(), dd.data_ptr(), n, loss.data_ptr())
+    g.sync()
+    want = (r0 - d).astype(np.float32)          # one FP32 subtraction per value
+    assert np.array_equal(r.cpu().numpy(), want)
+    ref = 0.5 * np.sum(want.astype(np.float64) ** 2)
+    got = float(loss[0])
+    assert abs(got - ref) <= 1e-12 * ref, (got, ref)
+    # the same residual again from the same inputs: the same bits
+    r2 = torch.from_numpy(r0).cuda()
+    _capi.cg_md_residual(g._h, r2.data_ptr(), dd.data_ptr(), n, loss[1:].data_ptr())
+    g.sync()
+    assert float(loss[1]) == got
+    # update with NaN gradient entries
+    m0 = rng.standard_normal(n).astype(np.float32)
+    gr = rng.standard_normal(n).astype(np.float32)
+    gr[::97] = np.nan
+    m = torch.from_numpy(m0).cuda()
+    grd = torch.from_numpy(gr).cuda()
+    alpha = 0.37
+    _capi.cg_md_update(g._h, m.data_ptr(), grd.data_ptr(), alpha, n)
+    g.sync()
+    g0 = np.where(np.isnan(gr), 0.0, gr).astype(np.float64)
+    mref = m0.astype(np.float64) - np.float64(np.float32(alpha)) * g0
+    assert np.max(np.abs(m.cpu().numpy() - mref)) <= 1e-6 * (1 + np.max(np.abs(mref)))
+    assert np.array_equal(m.cpu().numpy()[::97], m0[::97])
+    # errors
+    with pytest.raises(_capi.CygridError) as ei:
+        _capi.cg_md_update(g._h, m.data_ptr(), grd.data_ptr(), float("nan"), n)
+    assert ei.value.status == _capi.CG_EINVAL
+    with pytest.raises(_capi.CygridError) as ei:
+        _capi.cg_md_residual(g._h, None, dd.data_ptr(), n, loss.data_ptr())
+    assert ei.value.status == _capi.CG_EINVAL
+    g.close()

@@ -12,7 +12,9 @@ sampled target, found by a latitude-band prefilter that is a superset):
   non-increasing 50-step map-making loss;
 * the paper's Example 1 (1e8 samples) and its Appendix A.1 sight-line
   simulation (4.7e7 samples onto the 3,145,728 pixel centres of an nside-512
-  HEALPix grid).
+  HEALPix grid);
+* the bench's 64-job batch, captured fused, every job on sampled targets, in
+  the FP32 form and in the mixed form (BF16 tensor cores for C >= 16).
 """
 import json
 import os
@@ -202,3 +204,55 @@ def test_paper_sightline_a1_full_sampled():
     tsel = np.unique(np.concatenate([_sampled_targets(wl, 24, 611), [0, lon_t.size - 1]]))
     ref, _ = oracle_on_targets(wl, tsel, oracle.gauss1d(kern["sigma"], support))
     compare_maps(out_np[tsel], w_np[tsel], ref, tol=FP32_TOL)
+
+
+@pytest.mark.parametrize("form", ["fp32", "mixed"])
+def test_batch_config4_fused_every_job(form):
+    """The bench's 64-job batch (1.26e7 samples, 3.0e9 channel values, grids
+    64^2 .. 1024^2, sigma U[1', 8']) captured fused: every job against the
+    FP64 oracle on 24 sampled targets (the samples within reach of them).
+    FP32 form: FP32 data on the FP32 gridder, 1e-5 of S.  Mixed form: BF16
+    data for C >= 16 on the tensor cores (hi + lo weights), against the
+    oracle on the caller's unrounded FP32 data, within the BF16 data-rounding
+    bound (unit roundoff 2^-8) plus the 5e-5 of the weights; the C = 1 jobs
+    stay FP32 (1e-5)."""
+    import torch
+    from paper_1604_06667_gb300 import Batch, Gridder, _capi
+    dev = torch.device("cuda")
+    specs = workloads.batch_specs(64)
+    jobs, meta = [], []
+    for sp in specs:
+        lon, lat, d32, lon_t, lat_t = workloads.batch_job_device(sp, dev)
+        g = Gridder(lon_t, lat_t, n_channels=sp["C"], device=dev)
+        g.set_kernel("gauss1d", (sp["sigma"],), 3.0 * sp["sigma"], sp["sigma"] / 2.0)
+        tc = form == "mixed" and sp["C"] >= 16
+        g.set_path(_capi.CG_PATH_TC if tc else _capi.CG_PATH_FP32)
+        d = d32.to(torch.bfloat16) if tc else d32
+        out = torch.empty((g.n_targets, sp["C"]), device=dev)
+        w = torch.empty(g.n_targets, device=dev)
+        jobs.append((g, lon, lat, d, out, w))
+        meta.append((sp, lon, lat, d32, lon_t, lat_t, tc))
+    b = Batch(jobs).set_fused(True).capture()
+    b.run()
+    b.sync()
+    worst = {}
+    for j, ((g, _, _, _, out, w), (sp, lon, lat, d32, lon_t, lat_t, tc)) in enumerate(zip(jobs, meta)):
+        rng = np.random.Generator(np.random.PCG64(9000 + j))
+        tsel = np.sort(rng.choice(lon_t.size, size=min(24, lon_t.size), replace=False))
+        sigma = sp["sigma"]
+        cand = candidates_near(lon_t[tsel], lat_t[tsel], lon, lat, 3.0 * sigma)
+        rows = torch.from_numpy(cand).to(dev)
+        dref = d32[rows].double().cpu().numpy()
+        ref = oracle.grid_bruteforce(lon_t[tsel], lat_t[tsel], lon[cand], lat[cand], dref,
+                                     oracle.gauss1d(sigma, 3.0 * sigma))
+        tol = (2.0 ** -8 + 5e-5) if tc else FP32_TOL
+        ts = torch.from_numpy(tsel).to(dev)
+        me, mw = compare_maps(out[ts].cpu().numpy(), w[ts].cpu().numpy(), ref, tol=tol,
+                              wtol=5e-5 if tc else FP32_TOL)
+        key = "tc" if tc else "fp32"
+        worst[key] = max(worst.get(key, 0.0), me)
+    print("batch config 4 (%s form): largest error in units of S by gridder form: %s"
+          % (form, {k: "%.2e" % v for k, v in worst.items()}))
+    b.close()
+    for jb in jobs:
+        jb[0].close()

@@ -383,6 +383,9 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_block(
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t run[kRadix];
   __shared__ uint32_t warp_sums[kWarps];
+  __shared__ uint32_t t_start[kRadix];      // the tile's keys before digit d
+  __shared__ uint32_t s_key[kOsTile];       // the tile in sorted order
+  __shared__ uint32_t s_val[kOsTile];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_b = atomicAdd(ticket, 1u);
   cnt[tid] = 0;
@@ -404,11 +407,12 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_block(
     }
   }
   __syncthreads();
-  // global exclusive offset of digit tid
+  // global exclusive offset of digit tid, and the tile's own
   uint32_t tot;
   const uint32_t g_excl = block_exclusive_scan(ghist[tid], warp_sums, tot);
-  // publish the count, look back for the prefix, publish the prefix
   const uint32_t c = cnt[tid];
+  t_start[tid] = block_exclusive_scan(c, warp_sums, tot);
+  // publish the count, look back for the prefix, publish the prefix
   volatile uint64_t* st = status;
   if (b == 0) {
     st[(size_t)tid] = os_word(epoch, kInc, c);
@@ -451,7 +455,9 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_block(
     blk_off[tid] = g_excl + prefix;
   }
   __syncthreads();
-  // stable ranks in (item, thread) order and scatter
+  // stable ranks in (item, thread) order: the tile sorted in shared memory,
+  // then written out in runs per digit (consecutive threads, consecutive
+  // positions), instead of one scattered 4-byte store per key
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int it = 0; it < kOsItems; ++it) {
@@ -477,11 +483,19 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_block(
     }
     __syncthreads();
     if (valid) {
-      const uint32_t pos = blk_off[d] + wcnt[wid][d] + rank;
-      kout[pos] = k_it[it];
-      vout[pos] = v_it[it];
+      const uint32_t lp = t_start[d] + wcnt[wid][d] + rank;
+      s_key[lp] = k_it[it];
+      s_val[lp] = v_it[it];
     }
     __syncthreads();   // wcnt is cleared for the next item
+  }
+  const int n_tile = (int)((n - base) < kOsTile ? (n - base) : kOsTile);
+  for (int lp = tid; lp < n_tile; lp += kThreads) {
+    const uint32_t k = s_key[lp];
+    const uint32_t d = (k >> shift) & 0xffu;
+    const uint32_t pos = blk_off[d] + ((uint32_t)lp - t_start[d]);
+    kout[pos] = k;
+    vout[pos] = s_val[lp];
   }
 }
 

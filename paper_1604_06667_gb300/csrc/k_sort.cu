@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_warp(
   __shared__ uint32_t blk_off[kRadix];
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t warp_sums[kWarps];
+  __shared__ uint32_t t_start[kRadix];      // the tile's keys before digit d
+  __shared__ uint32_t s_key[kOsTile];       // the tile in sorted order
+  __shared__ uint32_t s_val[kOsTile];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_b = atomicAdd(ticket, 1u);
 #pragma unroll
@@ -310,9 +313,10 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_warp(
     wcnt[w2][tid] = c;
     c += x;
   }
-  // global exclusive offset of digit tid
+  // global exclusive offset of digit tid, and the tile's own
   uint32_t tot;
   const uint32_t g_excl = block_exclusive_scan(ghist[tid], warp_sums, tot);
+  t_start[tid] = block_exclusive_scan(c, warp_sums, tot);
   // publish the count, look back for the prefix, publish the prefix
   volatile uint64_t* st = status;
   if (b == 0) {
@@ -355,17 +359,30 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_warp(
     st[(size_t)b * kRadix + tid] = os_word(epoch, kInc, prefix + c);
     blk_off[tid] = g_excl + prefix;
   }
-  __syncthreads();
+  // the tile in sorted order in shared memory, then written out in runs per
+  // digit (consecutive threads, consecutive positions)
 #pragma unroll
   for (int it = 0; it < kOsItems; ++it) {
     if (wbase + it * 32 + lane < n) {
       const unsigned d = (k_it[it] >> shift) & 0xffu;
-      const uint32_t pos = blk_off[d] + wc[d] + r_it[it];
-      kout[pos] = k_it[it];
-      vout[pos] = v_it[it];
+      const uint32_t lp = t_start[d] + wc[d] + r_it[it];
+      s_key[lp] = k_it[it];
+      s_val[lp] = v_it[it];
     }
   }
+  __syncthreads();
+  const int64_t tbase = b * kOsTile;
+  const int n_tile = (int)((n - tbase) < kOsTile ? (n - tbase) : kOsTile);
+  for (int lp = tid; lp < n_tile; lp += kThreads) {
+    const uint32_t k = s_key[lp];
+    const uint32_t d = (k >> shift) & 0xffu;
+    const uint32_t pos = blk_off[d] + ((uint32_t)lp - t_start[d]);
+    kout[pos] = k;
+    vout[pos] = s_val[lp];
+  }
 }
+
+
 
 // One pass, ranked block-wide (for inputs of many waves of tiles): the
 // tile's digit counts come from a shared histogram, the look-back publishes

@@ -140,6 +140,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
                "r"(src_bytes)
                : "memory");
 }
+// 4-byte asynchronous global -> shared copy (scalar rows); src_bytes 0 fills zeros.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -188,9 +194,13 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
 
   const DT* data = static_cast<const DT*>(a.data);
   const int C = a.C;
-  // FP32 rows in 16-byte pieces go straight to shared memory (cp.async);
-  // BF16 rows and unaligned rows through registers
-  const bool async_rows = a.vec4 && sizeof(DT) == 4;
+  // shapes of at most 8 channels per thread are latency-bound: they load the
+  // candidate records of chunk q + 2 into registers while chunk q is
+  // computed, and copy unaligned FP32 rows asynchronously element by element
+  constexpr bool kPrefetch = CB <= 8;
+  // FP32 rows go straight to shared memory (cp.async: 16-byte pieces when
+  // aligned); BF16 rows and the wide shapes' unaligned rows through registers
+  const bool async_rows = sizeof(DT) == 4 && (a.vec4 || kPrefetch);
   const int64_t r0 = a.range_off[tile], r1 = a.range_off[tile + 1];
   // this CTA's share [c_lo, c_hi) of the tile's candidates (whole chunks)
   int c_lo = 0, c_hi = 0x7fffffff;
@@ -235,35 +245,42 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
     const int n_chunks = (v_hi - v_lo + K - 1) / K;
     if (n_chunks == 0) continue;
 
-    // candidates of the chunk at v0 into stage st (threads tid < K)
-    auto stage_cands = [&](int v0, int st) {
-      if (tid < K) {
-        const int v = v0 + tid;
-        if (v < v_hi) {
-          int lo = 0, hi = nr - 1;  // last range with rg_pre <= v
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
-          }
-          const int64_t s = S.rg[lo].x + (v - S.rg_pre[lo]);
-          const float4 h = a.s_hi[s], l = a.s_lo[s];
-          // the candidate relative to the tile centre, once for all targets
-          S.b[st][tid] = make_float4(df_diff(h.x, l.x, chi.x, clo.x),
-                                     df_diff(h.y, l.y, chi.y, clo.y),
-                                     df_diff(h.z, l.z, chi.z, clo.z), h.w);
-          S.idx[st][tid] = a.perm[s];
-        } else {
-          // padding candidate (never equal to an empty target slot's sentinel)
-          S.b[st][tid] = make_float4(df_diff(-4.f, 0.f, chi.x, clo.x),
-                                     df_diff(-4.f, 0.f, chi.y, clo.y),
-                                     df_diff(-4.f, 0.f, chi.z, clo.z), 0.f);
-          S.idx[st][tid] = 0xffffffffu;
+    // the record of candidate v0 + tid (threads tid < K): loads only
+    struct Cand {
+      float4 h, l;
+      uint32_t idx;
+    };
+    auto fetch_cand = [&](int v0) {
+      // padding candidate (never equal to an empty target slot's sentinel)
+      Cand c{make_float4(-4.f, -4.f, -4.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), 0xffffffffu};
+      const int v = v0 + tid;
+      if (tid < K && v < v_hi) {
+        int lo = 0, hi = nr - 1;  // last range with rg_pre <= v
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (S.rg_pre[mid] <= v) lo = mid; else hi = mid - 1;
         }
+        const int64_t s = S.rg[lo].x + (v - S.rg_pre[lo]);
+        c.h = a.s_hi[s];
+        c.l = a.s_lo[s];
+        c.idx = a.perm[s];
+      }
+      return c;
+    };
+    // a fetched record into stage st: the candidate relative to the tile
+    // centre, once for all targets
+    auto put_cand = [&](const Cand& c, int st) {
+      if (tid < K) {
+        S.b[st][tid] = make_float4(df_diff(c.h.x, c.l.x, chi.x, clo.x),
+                                   df_diff(c.h.y, c.l.y, chi.y, clo.y),
+                                   df_diff(c.h.z, c.l.z, chi.z, clo.z), c.h.w);
+        S.idx[st][tid] = c.idx;
       }
     };
+    auto stage_cands = [&](int v0, int st) { put_cand(fetch_cand(v0), st); };
     // channel rows of stage st's candidates (their indices are visible)
     auto stage_rows = [&](int st) {
-      if (async_rows) {
+      if (async_rows && a.vec4) {
         for (int e = tid; e < K * (CPAD / 4); e += NTH) {
           const int k = e / (CPAD / 4);
           const int c = (e % (CPAD / 4)) * 4;
@@ -294,6 +311,23 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
         }
       }
     };
+    // FP32 rows of any alignment, asynchronously (4-byte elements when the
+    // rows are not 16-byte aligned)
+    auto stage_rows_async = [&](int st) {
+      if (!kPrefetch || a.vec4) {
+        stage_rows(st);
+        return;
+      }
+      for (int e = tid; e < K * CPAD; e += NTH) {
+        const int k = e / CPAD;
+        const int c = e % CPAD;
+        const uint32_t idx = S.idx[st][k];
+        const bool ok = idx != 0xffffffffu && c_base + c < C;
+        const DT* src = ok ? data + (size_t)idx * C + c_base + c : data;
+        cp_async4(&S.d[st][k][c], src, ok ? 4 : 0);
+      }
+      cp_async_commit();
+    };
 
     // Two-stage pipeline, one barrier per chunk.  Chunk q uses stage q & 1.
     // Before the barrier of chunk q: the candidates of chunk q + 1 and the
@@ -302,11 +336,18 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
     // that follows its last reader.
     stage_cands(v_lo, 0);
     __syncthreads();
-    stage_rows(0);
+    if (async_rows) stage_rows_async(0); else stage_rows(0);
+    Cand pre;   // kPrefetch: the record of chunk q + 1, loaded one chunk ago
+    if (kPrefetch && n_chunks > 1) pre = fetch_cand(v_lo + K);
     for (int q = 0; q < n_chunks; ++q) {
       const int cur = q & 1, nxt = cur ^ 1;
       const bool more = q + 1 < n_chunks;
-      if (more) stage_cands(v_lo + (q + 1) * K, nxt);
+      if (kPrefetch) {
+        if (more) put_cand(pre, nxt);
+        if (q + 2 < n_chunks) pre = fetch_cand(v_lo + (q + 2) * K);
+      } else if (more) {
+        stage_cands(v_lo + (q + 1) * K, nxt);
+      }
 
       // ---- phase A: weights ----
 #pragma unroll 2
@@ -345,18 +386,25 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
             in = pair_inside_inl(a.tgt_ll[slot], a.sll[idx], a.kd.c2r_hi, a.kd.c2r_lo,
                                  a.kd.c2r_tol, a.kd.r_rad);
           }
-          if (in) ++npair; else w = -0.f;
+          if (in) {
+            ++npair;
+            // Neumaier (two-sum) accumulation of the weight map; a pair
+            // outside the support adds -0.0, which leaves (ws, wc) as they are
+            const float t = ws + w;
+            const float bp2 = t - ws;
+            wc += (ws - (t - bp2)) + (w - bp2);
+            ws = t;
+          } else {
+            w = -0.f;
+          }
         }
         S.w[cur][k][p] = w;
-        // Neumaier (two-sum) accumulation of the weight map
-        const float t = ws + w;
-        const float bp2 = t - ws;
-        wc += (ws - (t - bp2)) + (w - bp2);
-        ws = t;
       }
       if (async_rows) cp_async_wait_all();   // this thread's copies of chunk q
       __syncthreads();
-      if (more) stage_rows(nxt);
+      if (more) {
+        if (async_rows) stage_rows_async(nxt); else stage_rows(nxt);
+      }
 
       // ---- phase B: channel accumulation ----
 #pragma unroll 4
@@ -1245,7 +1293,7 @@ cudaError_t grid_f32_multi(const F32Multi& m, cudaStream_t s, int64_t* launches)
   cudaError_t e;
   switch (m.shape) {
     case 0: e = launch_multi<1, 4, 1, 12>(L, nsm, s); break;
-    case 1: e = launch_multi<1, 8, 1, 12>(L, nsm, s); break;
+    case 1: e = launch_multi<1, 8, 1, 10>(L, nsm, s); break;
     case 2: e = launch_multi<1, 8, 2, 6>(L, nsm, s); break;
     case 3: e = launch_multi<2, 8, 4, 5>(L, nsm, s); break;
     case 4: e = launch_multi<2, 16, 4, 4>(L, nsm, s); break;

@@ -121,7 +121,7 @@ struct alignas(16) F32Smem {
   static constexpr int CPAD = CB * NCG;
   float d[2][kChunk][CPAD];      // channel rows of the candidates
   float w[2][kChunk][kTile];     // weights w[k][p]
-  float4 b[2][kChunk];           // tile-relative candidate vector, omega in .w
+  float4 b[2][kChunk];           // tile-relative candidate vectors and omega (narrow shapes: pair-major, negated)
   uint32_t idx[2][kChunk];       // input index (0xffffffff: padding)
   int2 rg[kRangeBatch];          // a batch of the tile's sample ranges
   int rg_pre[kRangeBatch + 1];   // candidates before each range of the batch
@@ -198,6 +198,9 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
   // candidate records of chunk q + 2 into registers while chunk q is
   // computed, and copy unaligned FP32 rows asynchronously element by element
   constexpr bool kPrefetch = CB <= 8;
+  // narrow shapes: phase A on candidate pairs with packed f32x2 arithmetic
+  // (candidate vectors stored pair-major and negated)
+  constexpr bool kPairs = CB <= 8;
   // FP32 rows go straight to shared memory (cp.async: 16-byte pieces when
   // aligned); BF16 rows and the wide shapes' unaligned rows through registers
   const bool async_rows = sizeof(DT) == 4 && (a.vec4 || kPrefetch);
@@ -271,9 +274,21 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
     // centre, once for all targets
     auto put_cand = [&](const Cand& c, int st) {
       if (tid < K) {
-        S.b[st][tid] = make_float4(df_diff(c.h.x, c.l.x, chi.x, clo.x),
-                                   df_diff(c.h.y, c.l.y, chi.y, clo.y),
-                                   df_diff(c.h.z, c.l.z, chi.z, clo.z), c.h.w);
+        const float bx = df_diff(c.h.x, c.l.x, chi.x, clo.x);
+        const float by = df_diff(c.h.y, c.l.y, chi.y, clo.y);
+        const float bz = df_diff(c.h.z, c.l.z, chi.z, clo.z);
+        if constexpr (kPairs) {
+          // pair-major: (-x, -x', -y, -y'), (-z, -z', omega, omega') for the
+          // candidate pair (tid & ~1, tid | 1); target + (-candidate) is the
+          // target - candidate difference exactly
+          float* q = reinterpret_cast<float*>(&S.b[st][tid & ~1]) + (tid & 1);
+          q[0] = -bx;
+          q[2] = -by;
+          q[4] = -bz;
+          q[6] = c.h.w;
+        } else {
+          S.b[st][tid] = make_float4(bx, by, bz, c.h.w);
+        }
         S.idx[st][tid] = c.idx;
       }
     };
@@ -314,19 +329,21 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
     // FP32 rows of any alignment, asynchronously (4-byte elements when the
     // rows are not 16-byte aligned)
     auto stage_rows_async = [&](int st) {
-      if (!kPrefetch || a.vec4) {
-        stage_rows(st);
-        return;
+      if constexpr (kPrefetch) {
+        if (!a.vec4) {
+          for (int e = tid; e < K * CPAD; e += NTH) {
+            const int k = e / CPAD;
+            const int c = e % CPAD;
+            const uint32_t idx = S.idx[st][k];
+            const bool ok = idx != 0xffffffffu && c_base + c < C;
+            const DT* src = ok ? data + (size_t)idx * C + c_base + c : data;
+            cp_async4(&S.d[st][k][c], src, ok ? 4 : 0);
+          }
+          cp_async_commit();
+          return;
+        }
       }
-      for (int e = tid; e < K * CPAD; e += NTH) {
-        const int k = e / CPAD;
-        const int c = e % CPAD;
-        const uint32_t idx = S.idx[st][k];
-        const bool ok = idx != 0xffffffffu && c_base + c < C;
-        const DT* src = ok ? data + (size_t)idx * C + c_base + c : data;
-        cp_async4(&S.d[st][k][c], src, ok ? 4 : 0);
-      }
-      cp_async_commit();
+      stage_rows(st);
     };
 
     // Two-stage pipeline, one barrier per chunk.  Chunk q uses stage q & 1.
@@ -350,13 +367,20 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
       }
 
       // ---- phase A: weights ----
-#pragma unroll 2
-      for (int k = kk0; k < K; k += STEP) {
-        // the arithmetic of pair_weight, written out (pairs outside the
-        // support get -0.0)
-        const float4 sh = S.b[cur][k];
-        const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
-        const float c2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      // the arithmetic of pair_weight, written out, for candidate k at
+      // squared chord c2 (pairs outside the support get -0.0)
+      const float4* bp = S.b[cur];
+      // target - candidate k
+      auto diff = [&](int k) {
+        if constexpr (kPairs) {
+          const float* q = reinterpret_cast<const float*>(&bp[k & ~1]) + (k & 1);
+          return make_float3(at.x + q[0], at.y + q[2], at.z + q[4]);
+        } else {
+          const float4 sh = bp[k];
+          return make_float3(at.x - sh.x, at.y - sh.y, at.z - sh.z);
+        }
+      };
+      auto one = [&](int k, float c2, float om) {
         float w = -0.f;
         if (c2 <= a.kd.c2_out) {
           float d2;
@@ -370,13 +394,15 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
           if (a.kd.type == CG_GAUSS1D || a.kd.type == CG_TSINC) {
             ex = a.kd.k1 * d2;
           } else {
+            const float3 dv = diff(k);
+            const float dx = dv.x, dy = dv.y, dz = dv.z;
             const float ap = fmaf(dx, f1.x, fmaf(dy, f1.y, dz * f1.z));
             const float bp = fmaf(dx, f2.x, fmaf(dy, f2.y, dz * f2.z));
             const float s2 = fmaf(ap, ap, bp * bp);  // sin^2 d
             const float ratio = (s2 > 0.f) ? __fdividef(d2, s2) : 1.f;
             ex = fmaf(a.kd.k1 * ap, ap, a.kd.k2 * bp * bp) * ratio;
           }
-          w = ex2_approx(ex) * sh.w;
+          w = ex2_approx(ex) * om;
           if (a.kd.type == CG_TSINC) w *= sinc_pi(sqrtf(d2) * a.kd.inv_a);
           if (a.kd.dscale != 0.f) w *= d2 * a.kd.dscale;   // dw/dsigma pass
           bool in = true;
@@ -399,6 +425,29 @@ __device__ __forceinline__ void grid_item_f32(const GridArgs& a, F32Smem<PB, CB,
           }
         }
         S.w[cur][k][p] = w;
+      };
+      if constexpr (kPairs) {
+        // candidates in pairs (2 j, 2 j + 1): the difference vectors and the
+        // squared chords on packed f32x2 lanes, the same IEEE operations per lane
+        const float2 at_x2 = make_float2(at.x, at.x), at_y2 = make_float2(at.y, at.y),
+                     at_z2 = make_float2(at.z, at.z);
+#pragma unroll 1
+        for (int j = kk0; j < K / 2; j += STEP) {
+          const float4 xy = bp[2 * j], zo = bp[2 * j + 1];
+          const float2 dx = __fadd2_rn(at_x2, make_float2(xy.x, xy.y));
+          const float2 dy = __fadd2_rn(at_y2, make_float2(xy.z, xy.w));
+          const float2 dz = __fadd2_rn(at_z2, make_float2(zo.x, zo.y));
+          const float2 c2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          one(2 * j, c2.x, zo.z);
+          one(2 * j + 1, c2.y, zo.w);
+        }
+      } else {
+#pragma unroll 2
+        for (int k = kk0; k < K; k += STEP) {
+          const float4 sh = bp[k];
+          const float dx = at.x - sh.x, dy = at.y - sh.y, dz = at.z - sh.z;
+          one(k, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), sh.w);
+        }
       }
       if (async_rows) cp_async_wait_all();   // this thread's copies of chunk q
       __syncthreads();

@@ -217,16 +217,20 @@ __device__ __forceinline__ float df_floor(df32 a, float& frac) {
   return f;
 }
 
-// The belt part of ang2pix_ring_fast in double-float arithmetic (no FP64
-// operations): longitude lon (degrees, double-float, folded here), z = sin
-// lat as a double-float (|error| ~1e-14).  *ok = false outside the belt
-// (|z| >= 2/3 - 1e-9) or when a truncated quantity lies within the 1e-6
-// margin of an integer (df32 evaluates them to ~2^-48 relative, so the
-// decisions outside the margin are those of the FP64 definition).
-__device__ __forceinline__ int64_t ang2pix_ring_belt_df(int64_t ns, df32 lon, df32 z, bool* ok) {
+// ang2pix_ring_fast in double-float arithmetic (no FP64 operations):
+// longitude lon (degrees, double-float, folded here), z = sin lat as a
+// double-float (|error| ~1e-14).  *ok = false near the cap/belt boundary
+// (| |z| - 2/3 | <= 1e-6), within 1e-6 of a pole's z, at a quadrant boundary
+// of the caps, or when a truncated quantity lies within the 1e-6 margin of an
+// integer: df32 evaluates the truncated quantities (at most 4 nside = 65536)
+// to ~1e-8 absolute, so the decisions outside the margin are those of the
+// FP64 definition.
+__device__ __forceinline__ int64_t ang2pix_ring_df(int64_t ns, df32 lon, df32 z, bool* ok) {
   constexpr float M = 1e-6f;
+  constexpr float kZb = (float)(2.0 / 3.0);
   const float za = fabsf(z.hi);
-  if (!(za < (float)(2.0 / 3.0) - 1e-6f) || ns > 16384) {
+  const bool belt = za < kZb - 1e-6f;
+  if (!(belt || (za > kZb + 1e-6f && za < 1.f - 1e-6f)) || ns > 16384) {
     *ok = false;
     return 0;
   }
@@ -239,23 +243,53 @@ __device__ __forceinline__ int64_t ang2pix_ring_belt_df(int64_t ns, df32 lon, df
   }
   constexpr double kInv90 = 1.0 / 90.0;
   const df32 tt = df_mul(lon, df32{(float)kInv90, (float)(kInv90 - (double)(float)kInv90)});
-  const float dns = (float)ns;                           // a power of two or exact integer
-  df32 u = df_add(tt, df32{0.5f, 0.f});
-  u = df32{u.hi * dns, u.lo * dns};
-  const df32 v = df_mul(z, df32{0.75f * dns, 0.f});
-  const df32 A = df_add(u, df_neg(v)), B = df_add(u, v);
-  float fa, fb;
-  const float Af = df_floor(A, fa), Bf = df_floor(B, fb);
-  *ok = fa > M && fa < 1.f - M && fb > M && fb < 1.f - M;
-  const int64_t asc = (int64_t)Af;
-  const int64_t dsc = (int64_t)Bf;
-  int64_t k = ns + 1 + asc - dsc;
-  k = k < 1 ? 1 : (k > 2 * ns + 1 ? 2 * ns + 1 : k);
-  const int64_t odd = k & 1;
-  int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
-  j %= 4 * ns;
-  if (j < 0) j += 4 * ns;
-  return 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
+  const float dns = (float)ns;                           // exact: ns <= 16384
+  if (belt) {
+    // diamonds between ascending and descending edge lines
+    const df32 u = df_mul(df_add(tt, df32{0.5f, 0.f}), df32{dns, 0.f});
+    const df32 v = df_mul(z, df32{0.75f * dns, 0.f});
+    const df32 A = df_add(u, df_neg(v)), B = df_add(u, v);
+    float fa, fb;
+    const float Af = df_floor(A, fa), Bf = df_floor(B, fb);
+    *ok = fa > M && fa < 1.f - M && fb > M && fb < 1.f - M;
+    const int64_t asc = (int64_t)Af;
+    const int64_t dsc = (int64_t)Bf;
+    int64_t k = ns + 1 + asc - dsc;
+    k = k < 1 ? 1 : (k > 2 * ns + 1 ? 2 * ns + 1 : k);
+    const int64_t odd = k & 1;
+    int64_t j = (asc + dsc - ns + (1 - odd) + 1) / 2;
+    j %= 4 * ns;
+    if (j < 0) j += 4 * ns;
+    return 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
+  }
+  // polar caps: ring counted from the pole = sum of the two edge indices + 1,
+  // the edge indices from the fraction ft of the quadrant and
+  // x = nside sqrt(3 (1 - |z|))
+  float ftf;
+  const float tf = df_floor(tt, ftf);
+  const df32 ft = df_add(tt, df32{-tf, 0.f});             // tt - floor(tt), as a double-float
+  const df32 omft = df_add(df32{1.f, 0.f}, df_neg(ft));
+  const df32 zabs = z.hi < 0.f ? df_neg(z) : z;
+  const df32 w = df_mul(df32{3.f, 0.f}, df_add(df32{1.f, 0.f}, df_neg(zabs)));
+  // square root: FP32 estimate and one Newton step on the double-float residual
+  const float s0 = sqrtf(w.hi);
+  const df32 res = df_add(w, df_neg(df_two_prod(s0, s0)));
+  const df32 sq = df_fast_two_sum(s0, res.hi * (0.5f / s0));
+  const df32 x = df_mul(sq, df32{dns, 0.f});
+  const df32 P = df_mul(ft, x), Q = df_mul(omft, x);
+  float fp, fq;
+  const float Pf = df_floor(P, fp), Qf = df_floor(Q, fq);
+  bool good = ft.hi > 1e-12f && omft.hi > 1e-12f;
+  good = good && fp > M && fp < 1.f - M && fq > M && fq < 1.f - M;
+  const int64_t k = (int64_t)Pf + (int64_t)Qf + 1;
+  const df32 J = df_mul(tt, df32{(float)k, 0.f});           // k <= nside: exact in FP32
+  float fj;
+  const float Jf = df_floor(J, fj);
+  *ok = good && fj > M && fj < 1.f - M;
+  int64_t j = (int64_t)Jf;
+  j %= 4 * k;
+  if (j < 0) j += 4 * k;
+  return (z.hi > 0.f) ? 2 * k * (k - 1) + j : 12 * ns * ns - 2 * k * (k + 1) + j;
 }
 
 // RING index of a valid sample with z from the double-float sine; exact

@@ -93,9 +93,10 @@ __global__ void __launch_bounds__(32 * kQueryWarps) k_tile_query(
 // RING index of a valid direction and the double-float sine / cosine of its
 // latitude and longitude.  Ordinary angles (|lon| < 2048 deg) take an FP64-free
 // path: the inputs are split into double-float pairs with integer operations,
-// the trigonometry and the belt's index arithmetic run in double-float, and
-// only a decision within the margin of a pixel boundary, the polar caps and
-// the cap/belt boundary go to the FP64 routines.
+// the trigonometry and the index arithmetic run in double-float, and only a
+// decision within the margin of a pixel boundary, the cap/belt boundary, the
+// immediate neighbourhood of a pole and the caps' quadrant boundaries go to
+// the FP64 routines.
 __device__ __forceinline__ int64_t key_and_sincos(int64_t ns, double lo, double la, df32& sb,
                                                   df32& cb, df32& sl, df32& cl) {
   const bool fast = df_split_ok(lo) && df_split_ok(la) &&
@@ -106,7 +107,7 @@ __device__ __forceinline__ int64_t key_and_sincos(int64_t ns, double lo, double 
     const df32 lon_d = df_split(lo), lat_d = df_split(la);
     df_sincos_deg_df(lat_d, sb, cb);
     df_sincos_deg_df(lon_d, sl, cl);
-    kpix = ang2pix_ring_belt_df(ns, lon_d, sb, &ok);
+    kpix = ang2pix_ring_df(ns, lon_d, sb, &ok);
   } else {
     df_sincos_deg(la, sb, cb);
     df_sincos_deg(lo, sl, cl);

@@ -37,7 +37,7 @@ def adversarial(ns, rng):
     return np.array(lon), np.array(lat)
 
 
-@pytest.mark.parametrize("ns", [1, 2, 16, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("ns", [1, 2, 3, 16, 1000, 1024, 2048, 4096, 8192, 12345])
 def test_ang2pix_bit_exact(ns):
     from paper_1604_06667_gb300 import ang2pix_ring
     rng = np.random.Generator(np.random.PCG64(100 + ns))
@@ -59,7 +59,8 @@ def test_ang2pix_bit_exact(ns):
 @pytest.mark.parametrize("ns", [16, 1024, 4096, 8192])
 def test_sample_keys_bit_exact(ns):
     """The gridder's own per-sample keys (the double-float path for ordinary
-    angles, FP64 near boundaries, in the poles' caps and for |lon| >= 2048)
+    angles, FP64 near boundaries and pixel-edge or quadrant-edge values, near
+    the poles and for |lon| >= 2048)
     sorted and exported: equal to the oracle's sort of its keys."""
     import torch
     from paper_1604_06667_gb300 import Gridder

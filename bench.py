@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the differentiable-workload timings")
     ap.add_argument("--cpu-samples", type=int, default=12000)
+    ap.add_argument("--only", choices=["plain2d", "allsky", "example1"], default=None,
+                    help="time one other workload alone (at --scale; --form picks the form) "
+                         "and print its record instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -602,7 +605,7 @@ def time_config(args, dev, name):
     import torch
     import workloads
     from paper_1604_06667_gb300 import Gridder, _capi
-    wl = workloads.plain2d(1.0) if name == "plain2d" else workloads.allsky(1.0)
+    wl = workloads.plain2d(args.scale) if name == "plain2d" else workloads.allsky(args.scale)
     lon = torch.from_numpy(wl.lon_s).to(dev)
     lat = torch.from_numpy(wl.lat_s).to(dev)
     d32 = torch.from_numpy(wl.data).to(dev)
@@ -627,6 +630,8 @@ def time_config(args, dev, name):
         d16 = d32.to(torch.bfloat16)
         forms.append(("bf16", _capi.CG_PATH_TC, d16))
         forms.append(("bf16s", _capi.CG_PATH_TC_FAST, d16))
+    if args.form != "auto":
+        forms = [f for f in forms if f[0] == args.form]
     res = {"workload": "%s: %d samples x %d channels -> %d targets" % (
         name, wl.n_samples, wl.n_channels, wl.n_targets)}
     stream = torch.cuda.current_stream(dev)
@@ -663,7 +668,8 @@ def time_example1(args, dev):
     import torch
     import workloads
     from paper_1604_06667_gb300 import Gridder
-    lon, lat, data, lon_t, lat_t, kern, support, maxres = workloads.example1_device(dev)
+    lon, lat, data, lon_t, lat_t, kern, support, maxres = workloads.example1_device(
+        dev, n=max(1, int(round(100_000_000 * args.scale))))
     g = Gridder(lon_t, lat_t, n_channels=1, device=dev)
     g.set_kernel("gauss1d", (kern["sigma"],), support, maxres)
     out = torch.empty((g.n_targets, 1), device=dev)
@@ -853,6 +859,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     peaks, peaks_src = load_peaks()
+    if args.only:
+        progress("workload %s alone" % args.only)
+        r = time_example1(args, dev) if args.only == "example1" else \
+            time_config(args, dev, args.only)
+        print(json.dumps(strip_private(r), default=float))
+        return
     progress("generating workload")
     wl = workloads.cube(scale=args.scale)
     # headline: BF16 data with hi + lo BF16 weights; then single BF16

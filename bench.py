@@ -792,14 +792,8 @@ def study_aliasing(args, dev):
 
 def detail_path():
     """Where the full result record goes: BENCH_DETAIL if set, else
-    gpurun_out/bench_detail.json when that folder exists, else
     bench_detail.json in the working directory."""
-    p = os.environ.get("BENCH_DETAIL")
-    if p:
-        return p
-    if os.path.isdir(os.path.join(os.getcwd(), "gpurun_out")):
-        return os.path.join("gpurun_out", "bench_detail.json")
-    return "bench_detail.json"
+    return os.environ.get("BENCH_DETAIL") or "bench_detail.json"
 
 
 def compact_line(line, detail_file):

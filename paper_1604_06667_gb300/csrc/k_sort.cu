@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_os_pass_warp(
 // the tile's inclusive prefix before the ranking; then the keys are ranked
 // item by item (a round of 256 keys in (item, thread) order per step, warp
 // matches for equal digits, warps in order) and scattered.
-__global__ void __launch_bounds__(kThreads) k_os_pass_block(
+__global__ void __launch_bounds__(kThreads, 4) k_os_pass_block(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
     const uint32_t* __restrict__ ghist, uint64_t* status, uint32_t* ticket, uint32_t epoch,

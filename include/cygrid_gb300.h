@@ -103,9 +103,10 @@ cg_status cg_grid_create(cg_grid** out, const double* lon_deg, const double* lat
  *   params        host, [n_params]: {sigma}, {sigma_maj, sigma_min, PA} or {a, b},
  *                 degrees.
  *   support_deg   support radius r > 0: samples with d > r do not contribute.
- *   nside         internal HEALPix resolution (power of two, 1 .. 8192), or 0 to
- *                 derive it from hpx_maxres_deg: the smallest power of two with
- *                 pixel size sqrt(pi/3)/nside <= hpx_maxres_deg.
+ *   nside         internal HEALPix resolution, 1 .. 8192 (any integer; powers of
+ *                 two index a little faster), or 0 to derive it from
+ *                 hpx_maxres_deg: the smallest power of two with pixel size
+ *                 sqrt(pi/3)/nside <= hpx_maxres_deg.  Out of range: CG_EINVAL.
  * The result does not depend on nside (the cut d <= r is exact); nside only
  * changes how candidates are found.  Resets the accumulators.  Synchronising. */
 cg_status cg_set_kernel(cg_grid* g, int32_t kernel_type, const double* params,

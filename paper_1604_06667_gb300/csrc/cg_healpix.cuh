@@ -188,8 +188,11 @@ __device__ __forceinline__ int64_t ang2pix_ring_fast(int64_t ns, double lon_deg,
     pix = 2 * ns * (ns - 1) + (k - 1) * 4 * ns + j;
   } else {
     const double ft = tt - floor(tt);
-    // near a pole sqrt(1 - za) magnifies the error of z: leave it to FP64
-    good = good && ft > 1e-12 && ft < 1.0 - 1e-12 && 1.0 - za > 1e-6;
+    // near a pole sqrt(1 - za) magnifies the error of z (<= 1e-13): with
+    // 1 - za > 1e-5 the error of x stays below 0.5e-13 nside sqrt(3) /
+    // sqrt(1e-5) < 5e-7 for nside <= 16384, inside the margin; nearer the
+    // pole FP64 decides
+    good = good && ft > 1e-12 && ft < 1.0 - 1e-12 && 1.0 - za > 1e-5;
     const double x = dns * sqrt(3.0 * (1.0 - za));
     const double P = ft * x, Q = (1.0 - ft) * x;
     const double fp = P - floor(P), fq = Q - floor(Q);
@@ -220,7 +223,7 @@ __device__ __forceinline__ float df_floor(df32 a, float& frac) {
 // ang2pix_ring_fast in double-float arithmetic (no FP64 operations):
 // longitude lon (degrees, double-float, folded here), z = sin lat as a
 // double-float (|error| ~1e-14).  *ok = false near the cap/belt boundary
-// (| |z| - 2/3 | <= 1e-6), within 1e-6 of a pole's z, at a quadrant boundary
+// (| |z| - 2/3 | <= 1e-6), within 1e-5 of a pole's z, at a quadrant boundary
 // of the caps, or when a truncated quantity lies within the 1e-6 margin of an
 // integer: df32 evaluates the truncated quantities (at most 4 nside = 65536)
 // to ~1e-8 absolute, so the decisions outside the margin are those of the
@@ -230,7 +233,7 @@ __device__ __forceinline__ int64_t ang2pix_ring_df(int64_t ns, df32 lon, df32 z,
   constexpr float kZb = (float)(2.0 / 3.0);
   const float za = fabsf(z.hi);
   const bool belt = za < kZb - 1e-6f;
-  if (!(belt || (za > kZb + 1e-6f && za < 1.f - 1e-6f)) || ns > 16384) {
+  if (!(belt || (za > kZb + 1e-6f && za < 1.f - 1e-5f)) || ns > 16384) {
     *ok = false;
     return 0;
   }

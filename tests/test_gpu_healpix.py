@@ -23,6 +23,13 @@ def adversarial(ns, rng):
                   180.0, 270.0, -45.0):
             lon.append(l)
             lat.append(b)
+    # either side of the pole thresholds of the fast paths (1 - |z| = 1e-5,
+    # 1e-6), where the error of z is magnified most
+    for dz in (3e-5, 1.2e-5, 1e-5, 0.8e-5, 3e-6, 1e-6, 3e-7):
+        b = math.degrees(math.asin(1.0 - dz))
+        for l in rng.uniform(0.0, 360.0, 24):
+            lon += [l, l]
+            lat += [b, -b]
     # ring centres and pixel-centre / pixel-edge longitudes of a few rings
     for i in sorted(set([1, 2, ns - 1, ns, ns + 1, 2 * ns, 3 * ns, 3 * ns + 1, 4 * ns - 1])):
         if i < 1 or i > 4 * ns - 1:
